@@ -1,0 +1,218 @@
+/*
+ * kcs.h -- C ABI of the Kinetic Compressive Sensing hot path on one B300 GPU.
+ *
+ * The library implements the Iterated Conditional Modes loop of Scipioni et
+ * al., "Kinetic Compressive Sensing" (Sec. II-D): (a) the OS-MAP-OSL update of
+ * every frame's activity image with the kinetics-derived prior (Eq. 2-3) and
+ * (b) the voxel-parallel MAP Levenberg-Marquardt fit of the FDG two-tissue
+ * irreversible model under a Huber prior on the kinetic maps (Eq. 4-6).
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ *  - Every function returns an int status (KCS_OK = 0).  On failure the
+ *    thread-local text of kcs_last_error() says why; nothing has been
+ *    launched when the status is KCS_ERR_INVALID_ARG.
+ *  - Array arguments are DEVICE pointers owned by the caller, float32,
+ *    C-contiguous in the layouts stated below, 16-byte aligned; the library
+ *    never frees them and never keeps them beyond the call, except inside a
+ *    kcs_study_t, which stores the pointers its descriptor names (the caller
+ *    keeps them alive until kcs_destroy_study).
+ *  - Compute calls take a cudaStream_t (passed as void*, NULL = legacy default
+ *    stream), are asynchronous on that stream and allocate nothing; scratch
+ *    memory is passed in as a workspace whose size the *_workspace_size
+ *    functions report.  Only the create_* functions allocate (small tables).
+ *  - Layouts (Z planes, ny rows, nx columns, A angles, B bins, M frames):
+ *      image x, model TAC F       [Z][ny][nx][M]   (frames innermost)
+ *      sinogram (counts, randoms) [Z][A][B][M]     (angles in natural order)
+ *      subset sinogram            [Z][A_k][B][M]   (A_k angles of subset k)
+ *      kinetic maps               [4][Z][ny][nx]   (K1, k2, k3, Vb planes)
+ *      per-voxel scalars          [Z][ny][nx]
+ *    n_frames must be a multiple of 4 and at most 32.
+ *  - Time is in minutes; frame_dt are frame durations.
+ */
+#ifndef KCS_H
+#define KCS_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct kcs_geometry kcs_geometry_t;
+typedef struct kcs_kinetics kcs_kinetics_t;
+typedef struct kcs_study kcs_study_t;
+
+enum kcs_status {
+  KCS_OK = 0,
+  KCS_ERR_INVALID_ARG = 1,
+  KCS_ERR_CUDA = 2,
+  KCS_ERR_OOM = 3,
+  KCS_ERR_TIMEOUT = 4,
+  KCS_ERR_UNIMPLEMENTED = 5,
+  KCS_ERR_RANGE = 6
+};
+
+/* Layout of the randoms argument of the OSL calls. */
+enum kcs_randoms_layout {
+  KCS_RANDOMS_NONE = 0,      /* no randoms (pointer ignored)            */
+  KCS_RANDOMS_PER_FRAME = 1, /* float [M]: the same r_m in every bin     */
+  KCS_RANDOMS_FULL = 2       /* float [Z][A][B][M]                       */
+};
+
+/* Thread-local description of the last failure on this thread ("" if none). */
+const char* kcs_last_error(void);
+/* ABI version, incremented on any incompatible change. */
+int kcs_version(void);
+
+/* ---------------------------------------------------------------- geometry
+ * Parallel-beam stacked-2D geometry with a ray-driven Joseph projector; the
+ * system matrix p_vd of Eq. 2 (the paper leaves the projector unnamed).
+ * Voxel (i, j) has centre ((i-(nx-1)/2) h, (j-(ny-1)/2) h), h = vox_mm.
+ * Angle a has theta = a*pi/A; bin b has offset u = (b-(B-1)/2) bin_mm and
+ * the ray {p : p.(cos theta, sin theta) = u}.  Angles with A <= 4a <= 3A are
+ * sampled at every column (rows interpolated linearly), the others at every
+ * row; step weight h / max(|cos|,|sin|).  Ordered subset k holds the angles
+ * a = k, k+S, k+2S, ... (the "OS" of OS-MAP-OSL, Sec. I).
+ * Allocates a small per-angle table on the current device. */
+int kcs_create_geometry(kcs_geometry_t** out, int nx, int ny, int nz, float vox_mm,
+                        int n_bins, int n_angles, float bin_mm, int n_subsets);
+int kcs_destroy_geometry(kcs_geometry_t* g);
+/* Host copy of the angle indices of subset k (subset = -1: all angles).
+ * angles_out may be NULL to query the count only. */
+int kcs_geometry_subset_angles(const kcs_geometry_t* g, int subset, int* angles_out,
+                               int* n_out);
+
+/* y = P_k x: forward projection of every frame onto the rays of subset k
+ * (subset = -1: all angles).  x [Z][ny][nx][M] -> y [Z][A_k][B][M]
+ * (overwritten).  The weights are the geometric p_vd (no frame duration). */
+int kcs_forward_project(const kcs_geometry_t* g, int subset, int n_frames,
+                        const float* x, float* y, void* stream);
+/* x = P_k^T y: the exact transpose of kcs_forward_project (same (v, d, w)
+ * triples, gathered per voxel, no atomics).  y [Z][A_k][B][M] ->
+ * x [Z][ny][nx][M] (overwritten). */
+int kcs_back_project(const kcs_geometry_t* g, int subset, int n_frames,
+                     const float* y, float* x, void* stream);
+/* sens = sum_{d in S_k} n_d p_vd per voxel [Z][ny][nx] (bin_factor NULL: n_d = 1). */
+int kcs_sensitivity(const kcs_geometry_t* g, int subset, const float* bin_factor,
+                    float* sens, void* stream);
+
+/* -------------------------------------------------------- OS-MAP-OSL (a)
+ * One OS-MAP-OSL-KP update of every frame on subset k (Eq. 2 with the
+ * kinetics-derived prior of Eq. 3), in place on x:
+ *   ybar = kappa dt_m n_d (P x)_dm + r_dm,   rho = s / ybar (0 if ybar <= 0)
+ *   x <- x * kappa dt_m (P_k^T n rho)_vm
+ *          / max(kappa dt_m sens_v + (beta/S)(x - F)/sigma2, 1e-3 kappa dt_m sens_v)
+ * with sens_v = sum_{d in S_k} n_d p_vd; voxels with sens_v = 0 keep x.
+ * frame_dt [M] (device); counts and randoms in natural angle order (the
+ * subset's rows are read in place); bin_factor [Z][A][B] or NULL (n_d = 1);
+ * F_model [Z][ny][nx][M] or NULL (prior off; beta ignored).
+ * workspace >= kcs_osl_workspace_size bytes (holds rho of one subset). */
+size_t kcs_osl_workspace_size(const kcs_geometry_t* g, int n_frames);
+int kcs_osl_update(const kcs_geometry_t* g, int subset, int n_frames, const float* frame_dt,
+                   float kappa, const float* counts, const float* randoms, int randoms_layout,
+                   const float* bin_factor, const float* F_model, float beta_kp, float sigma2,
+                   float* x, void* workspace, size_t ws_bytes, void* stream);
+/* The two halves of kcs_osl_update, for callers that time or reuse them:
+ * kcs_osl_ratio writes rho = s / (kappa dt_m n_d (P_k x)_dm + r_dm) (0 where the
+ * denominator is <= 0) to rho [Z][A_k][B][M]; kcs_osl_backproject applies
+ * the multiplicative OSL update of x from that rho (Eq. 2-3). */
+int kcs_osl_ratio(const kcs_geometry_t* g, int subset, int n_frames, const float* frame_dt,
+                  float kappa, const float* counts, const float* randoms, int randoms_layout,
+                  const float* bin_factor, const float* x, float* rho, void* stream);
+int kcs_osl_backproject(const kcs_geometry_t* g, int subset, int n_frames, const float* frame_dt,
+                        float kappa, const float* bin_factor, const float* rho,
+                        const float* F_model, float beta_kp, float sigma2, float* x,
+                        void* stream);
+/* Uniform start image per frame: c_m = max(sum(s - r), 0) / (kappa dt_m sum(n P 1)),
+ * at least 1e-6, written to every voxel of x [Z][ny][nx][M].
+ * workspace >= kcs_osl_workspace_size bytes. */
+int kcs_init_image(const kcs_geometry_t* g, int n_frames, const float* frame_dt, float kappa,
+                   const float* counts, const float* randoms, int randoms_layout,
+                   const float* bin_factor, float* x, void* workspace, size_t ws_bytes,
+                   void* stream);
+
+/* ---------------------------------------------------------- kinetics
+ * FDG two-tissue irreversible model with blood fraction (Sec. III-A, IV-A),
+ * parameters (K1, k2, k3, Vb), a = k2 + k3, driven by the Feng plasma input
+ *   Cp(t) = (A1 t - A2 - A3) e^{-l1 t} + A2 e^{-l2 t} + A3 e^{-l3 t},
+ *   F_m = (1/dt_m) int_{frame m} [(1 - Vb) C_T + Vb Cp] dt,
+ * evaluated analytically (Sec. II-C): per interval the convolution with
+ * e^{-at} is e^{-aD} times a power series in a with non-negative coefficients
+ * (input moments over the interval) that this call tabulates once in float64
+ * on the device.  t_start, t_end: host arrays of n_frames frame limits
+ * (ordered, no overlap; gaps allowed); feng: host {A1, A2, A3, l1, l2, l3}.
+ * Valid for 0 <= k2 + k3 <= 3.5 per minute (the LM box reaches 3). */
+int kcs_create_kinetics(kcs_kinetics_t** out, int n_frames, const double* t_start,
+                        const double* t_end, const double* feng, void* stream);
+int kcs_destroy_kinetics(kcs_kinetics_t* k);
+
+/* F = model TACs of n_vox voxels: params [4][n_vox] -> F [n_vox][M];
+ * J [n_vox][M][4] (d/dK1, d/dk2, d/dk3, d/dVb) when not NULL. */
+int kcs_tac_eval(const kcs_kinetics_t* k, int64_t n_vox, const float* params, float* F,
+                 float* J, void* stream);
+/* Ki = K1 k3 / (k2 + k3) (0 where k2 + k3 = 0), Sec. IV-B: [4][n_vox] -> [n_vox]. */
+int kcs_ki(int64_t n_vox, const float* params, float* ki, void* stream);
+
+/* ------------------------------------------------------------ MAP-LM (b)
+ * Huber gradient dH/dxi_p = sum_{k in N8(v)} clamp(xi_p - xi_{k,p}, -delta, delta)
+ * over the in-plane 3x3 clique (Eq. 6, Sec. II-C), per map: [4][Z][ny][nx]. */
+int kcs_huber_grad(int nx, int ny, int nz, const float* params, float delta, float* grad,
+                   void* stream);
+/* n_steps synchronous MAP-LM steps (Eq. 4) of every voxel's TAC x [Z][ny][nx][M]:
+ *   (J^T J + lambda I) step = J^T (x - F) - beta_h dH/dxi      (solved in float64)
+ *   trial = clamp(xi + step, 0, (2, 2, 1, 1)); accept iff the voxel objective
+ *   1/2 |x - F|^2 + beta_h sum_p sum_{N8} huber(xi_p - xi_{k,p}) decreases,
+ *   with the neighbours frozen at their start-of-step values;
+ *   lambda /= 10 (>= 1e-7) on accept, *= 10 (<= 1e7) on reject.
+ * params [4][Z][ny][nx] in/out; lambda [Z][ny][nx] in/out, or NULL to start
+ * every voxel at 1e-2; F_out [Z][ny][nx][M] receives F(final params) when not
+ * NULL.  workspace >= kcs_lm_workspace_size(nx, ny, nz) bytes. */
+size_t kcs_lm_workspace_size(int nx, int ny, int nz);
+int kcs_map_lm_fit(const kcs_kinetics_t* k, int nx, int ny, int nz, const float* x,
+                   float* params, float* lambda, int n_steps, float beta_h, float delta,
+                   float* F_out, void* workspace, size_t ws_bytes, void* stream);
+
+/* --------------------------------------------------------------- ICM
+ * A study binds a geometry, a kinetics table and the caller's device buffers;
+ * kcs_icm_iterate runs Sec. II-D's alternation on it, all on one stream:
+ *   for each iteration: one OSL pass over subsets 0..S-1 (prior built from
+ *   F = F(params) when an earlier iteration ran or params_given is set),
+ *   then n_lm MAP-LM steps warm-started from params (lambda reset to 1e-2),
+ *   then F <- F(params).
+ * x must hold a start image (e.g. from kcs_init_image); params must hold the
+ * start maps. */
+typedef struct kcs_study_desc {
+  const kcs_geometry_t* geom;
+  const kcs_kinetics_t* kin;
+  int n_frames;
+  float kappa;             /* count calibration: counts per (activity . mm . min) */
+  const float* frame_dt;   /* [M] device                                      */
+  const float* counts;     /* [Z][A][B][M]                                    */
+  const float* randoms;    /* see randoms_layout                              */
+  int randoms_layout;
+  const float* bin_factor; /* [Z][A][B] or NULL                               */
+  float* x;                /* [Z][ny][nx][M] in/out                           */
+  float* params;           /* [4][Z][ny][nx] in/out                           */
+  float* F;                /* [Z][ny][nx][M] out (model TACs of params)       */
+  int params_given;        /* nonzero: prior on from the first iteration      */
+  int n_lm;                /* MAP-LM steps per iteration                      */
+  float beta_kp, sigma2;   /* kinetics-derived prior (Eq. 3)                  */
+  float beta_h, delta;     /* Huber prior (Eq. 4-6)                           */
+  void* workspace;         /* >= kcs_study_workspace_size bytes               */
+  size_t ws_bytes;
+} kcs_study_desc_t;
+
+size_t kcs_study_workspace_size(const kcs_geometry_t* g, int n_frames);
+int kcs_create_study(kcs_study_t** out, const kcs_study_desc_t* desc);
+int kcs_destroy_study(kcs_study_t* st);
+/* Run n_iter ICM iterations (asynchronous on stream). */
+int kcs_icm_iterate(kcs_study_t* st, int n_iter, void* stream);
+/* Number of ICM iterations issued so far on this study. */
+int kcs_study_iterations(const kcs_study_t* st);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* KCS_H */

@@ -1,0 +1,303 @@
+"""Thin torch-facing wrappers of the kcs C ABI (argument marshalling only).
+
+Every array is a CUDA float32 tensor in the layout the C header states; the
+wrappers check device, dtype, shape and contiguity, pass raw pointers and the
+current torch stream, and raise KcsError on a non-zero status.  All arithmetic
+runs in libkcs.so's kernels.
+"""
+from __future__ import annotations
+
+import ctypes as C
+
+import numpy as np
+import torch
+
+from ._lib import StudyDesc, check, lib
+
+RANDOMS_NONE, RANDOMS_PER_FRAME, RANDOMS_FULL = 0, 1, 2
+
+
+def _stream():
+    return C.c_void_p(torch.cuda.current_stream().cuda_stream)
+
+
+def _ptr(t, name, shape=None, dtype=torch.float32, allow_none=False):
+    if t is None:
+        if allow_none:
+            return None
+        raise ValueError(f"{name} is required")
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise ValueError(f"{name} must be a CUDA tensor")
+    if t.dtype != dtype:
+        raise ValueError(f"{name} must be {dtype}, got {t.dtype}")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+    if shape is not None and tuple(t.shape) != tuple(shape):
+        raise ValueError(f"{name} has shape {tuple(t.shape)}, expected {tuple(shape)}")
+    return C.c_void_p(t.data_ptr())
+
+
+def _workspace(nbytes, device):
+    return torch.empty(max(int(nbytes), 1), dtype=torch.uint8, device=device)
+
+
+class Geometry:
+    """Parallel-beam stacked-2D Joseph geometry with S ordered subsets."""
+
+    def __init__(self, nx, ny, nz, vox_mm, n_bins, n_angles, bin_mm, n_subsets):
+        h = C.c_void_p()
+        check(lib.kcs_create_geometry(C.byref(h), nx, ny, nz, vox_mm, n_bins, n_angles, bin_mm,
+                                      n_subsets))
+        self.handle = h
+        self.nx, self.ny, self.nz = nx, ny, nz
+        self.vox_mm, self.bin_mm = vox_mm, bin_mm
+        self.n_bins, self.n_angles, self.n_subsets = n_bins, n_angles, n_subsets
+        self._sub = {}
+
+    def subset_angles(self, k):
+        if k not in self._sub:
+            n = C.c_int()
+            check(lib.kcs_geometry_subset_angles(self.handle, k, None, C.byref(n)))
+            out = (C.c_int * n.value)()
+            check(lib.kcs_geometry_subset_angles(self.handle, k, out, C.byref(n)))
+            self._sub[k] = np.array(out[:], dtype=np.int64)
+        return self._sub[k]
+
+    def n_sub(self, k):
+        return len(self.subset_angles(k))
+
+    def image_shape(self, M):
+        return (self.nz, self.ny, self.nx, M)
+
+    def sino_shape(self, M, k=-1):
+        return (self.nz, self.n_angles if k < 0 else self.n_sub(k), self.n_bins, M)
+
+    def close(self):
+        if getattr(self, "handle", None):
+            lib.kcs_destroy_geometry(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        self.close()
+
+
+def forward_project(g: Geometry, x, subset=-1, out=None):
+    """y = P_k x for every frame: [Z][ny][nx][M] -> [Z][A_k][B][M]."""
+    M = x.shape[-1]
+    px = _ptr(x, "x", g.image_shape(M))
+    if out is None:
+        out = torch.empty(g.sino_shape(M, subset), device=x.device, dtype=torch.float32)
+    py = _ptr(out, "out", g.sino_shape(M, subset))
+    check(lib.kcs_forward_project(g.handle, subset, M, px, py, _stream()))
+    return out
+
+
+def back_project(g: Geometry, y, subset=-1, out=None):
+    """x = P_k^T y for every frame: [Z][A_k][B][M] -> [Z][ny][nx][M]."""
+    M = y.shape[-1]
+    py = _ptr(y, "y", g.sino_shape(M, subset))
+    if out is None:
+        out = torch.empty(g.image_shape(M), device=y.device, dtype=torch.float32)
+    px = _ptr(out, "out", g.image_shape(M))
+    check(lib.kcs_back_project(g.handle, subset, M, py, px, _stream()))
+    return out
+
+
+def sensitivity(g: Geometry, subset=-1, bin_factor=None, device="cuda"):
+    out = torch.empty((g.nz, g.ny, g.nx), device=device, dtype=torch.float32)
+    pb = _ptr(bin_factor, "bin_factor", (g.nz, g.n_angles, g.n_bins), allow_none=True)
+    check(lib.kcs_sensitivity(g.handle, subset, pb, _ptr(out, "sens"), _stream()))
+    return out
+
+
+def _randoms(g, randoms, M):
+    if randoms is None:
+        return None, RANDOMS_NONE
+    if randoms.dim() == 1:
+        return _ptr(randoms, "randoms", (M,)), RANDOMS_PER_FRAME
+    return _ptr(randoms, "randoms", g.sino_shape(M)), RANDOMS_FULL
+
+
+def osl_workspace_size(g: Geometry, M):
+    return lib.kcs_osl_workspace_size(g.handle, M)
+
+
+def osl_update(g: Geometry, subset, x, frame_dt, kappa, counts, randoms=None, bin_factor=None,
+               F=None, beta=0.0, sigma2=1.0, workspace=None):
+    """One OS-MAP-OSL-KP update of x (in place) on subset k."""
+    M = x.shape[-1]
+    pr, layout = _randoms(g, randoms, M)
+    if workspace is None:
+        workspace = _workspace(osl_workspace_size(g, M), x.device)
+    check(lib.kcs_osl_update(
+        g.handle, subset, M, _ptr(frame_dt, "frame_dt", (M,)), float(kappa),
+        _ptr(counts, "counts", g.sino_shape(M)), pr, layout,
+        _ptr(bin_factor, "bin_factor", (g.nz, g.n_angles, g.n_bins), allow_none=True),
+        _ptr(F, "F", g.image_shape(M), allow_none=True), float(beta), float(sigma2),
+        _ptr(x, "x", g.image_shape(M)), C.c_void_p(workspace.data_ptr()), workspace.numel(),
+        _stream()))
+    return x
+
+
+def osl_ratio(g: Geometry, subset, x, frame_dt, kappa, counts, randoms=None, bin_factor=None,
+              out=None):
+    """rho = s / ybar on the rays of subset k: [Z][A_k][B][M]."""
+    M = x.shape[-1]
+    pr, layout = _randoms(g, randoms, M)
+    if out is None:
+        out = torch.empty(g.sino_shape(M, subset), device=x.device, dtype=torch.float32)
+    check(lib.kcs_osl_ratio(
+        g.handle, subset, M, _ptr(frame_dt, "frame_dt", (M,)), float(kappa),
+        _ptr(counts, "counts", g.sino_shape(M)), pr, layout,
+        _ptr(bin_factor, "bin_factor", (g.nz, g.n_angles, g.n_bins), allow_none=True),
+        _ptr(x, "x", g.image_shape(M)), _ptr(out, "rho", g.sino_shape(M, subset)), _stream()))
+    return out
+
+
+def osl_backproject(g: Geometry, subset, x, frame_dt, kappa, rho, bin_factor=None, F=None,
+                    beta=0.0, sigma2=1.0):
+    """OSL update of x (in place) from a ratio sinogram rho of subset k."""
+    M = x.shape[-1]
+    check(lib.kcs_osl_backproject(
+        g.handle, subset, M, _ptr(frame_dt, "frame_dt", (M,)), float(kappa),
+        _ptr(bin_factor, "bin_factor", (g.nz, g.n_angles, g.n_bins), allow_none=True),
+        _ptr(rho, "rho", g.sino_shape(M, subset)), _ptr(F, "F", g.image_shape(M), allow_none=True),
+        float(beta), float(sigma2), _ptr(x, "x", g.image_shape(M)), _stream()))
+    return x
+
+
+def init_image(g: Geometry, frame_dt, kappa, counts, randoms=None, bin_factor=None, out=None,
+               workspace=None):
+    """Uniform per-frame start image matching the measured trues."""
+    M = counts.shape[-1]
+    pr, layout = _randoms(g, randoms, M)
+    if out is None:
+        out = torch.empty(g.image_shape(M), device=counts.device, dtype=torch.float32)
+    if workspace is None:
+        workspace = _workspace(osl_workspace_size(g, M), counts.device)
+    check(lib.kcs_init_image(
+        g.handle, M, _ptr(frame_dt, "frame_dt", (M,)), float(kappa),
+        _ptr(counts, "counts", g.sino_shape(M)), pr, layout,
+        _ptr(bin_factor, "bin_factor", (g.nz, g.n_angles, g.n_bins), allow_none=True),
+        _ptr(out, "out", g.image_shape(M)), C.c_void_p(workspace.data_ptr()), workspace.numel(),
+        _stream()))
+    return out
+
+
+class Kinetics:
+    """Frame schedule + Feng input; tabulates the model's series coefficients."""
+
+    def __init__(self, t_start, t_end, feng):
+        ts = np.ascontiguousarray(t_start, dtype=np.float64)
+        te = np.ascontiguousarray(t_end, dtype=np.float64)
+        fe = np.array([feng["A1"], feng["A2"], feng["A3"], feng["l1"], feng["l2"], feng["l3"]],
+                      dtype=np.float64)
+        h = C.c_void_p()
+        dptr = C.POINTER(C.c_double)
+        check(lib.kcs_create_kinetics(C.byref(h), len(ts), ts.ctypes.data_as(dptr),
+                                      te.ctypes.data_as(dptr), fe.ctypes.data_as(dptr), _stream()))
+        self.handle = h
+        self.M = len(ts)
+        self.t_start, self.t_end = ts, te
+
+    def close(self):
+        if getattr(self, "handle", None):
+            lib.kcs_destroy_kinetics(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        self.close()
+
+
+def tac_eval(kin: Kinetics, params, jacobian=False, out=None):
+    """params [4][...] -> F [...][M] (and J [...][M][4])."""
+    shp = tuple(params.shape[1:])
+    n = int(np.prod(shp)) if shp else 1
+    F = out if out is not None else torch.empty(shp + (kin.M,), device=params.device,
+                                                dtype=torch.float32)
+    J = torch.empty(shp + (kin.M, 4), device=params.device, dtype=torch.float32) if jacobian else None
+    check(lib.kcs_tac_eval(kin.handle, n, _ptr(params, "params"), _ptr(F, "F", shp + (kin.M,)),
+                           _ptr(J, "J", allow_none=True), _stream()))
+    return (F, J) if jacobian else F
+
+
+def ki(params):
+    """Ki = K1 k3 / (k2 + k3) per voxel."""
+    shp = tuple(params.shape[1:])
+    out = torch.empty(shp, device=params.device, dtype=torch.float32)
+    check(lib.kcs_ki(out.numel(), _ptr(params, "params"), _ptr(out, "ki"), _stream()))
+    return out
+
+
+def huber_grad(params, delta):
+    _, nz, ny, nx = params.shape
+    out = torch.empty_like(params)
+    check(lib.kcs_huber_grad(nx, ny, nz, _ptr(params, "params"), float(delta), _ptr(out, "grad"),
+                             _stream()))
+    return out
+
+
+def lm_workspace_size(nx, ny, nz):
+    return lib.kcs_lm_workspace_size(nx, ny, nz)
+
+
+def map_lm_fit(kin: Kinetics, x, params, n_steps, beta_h, delta, lam=None, F_out=None,
+               workspace=None):
+    """n_steps MAP-LM steps on params [4][Z][Y][X] (in place) for TACs x [Z][Y][X][M]."""
+    nz, ny, nx, M = x.shape
+    if workspace is None:
+        workspace = _workspace(lm_workspace_size(nx, ny, nz), x.device)
+    check(lib.kcs_map_lm_fit(
+        kin.handle, nx, ny, nz, _ptr(x, "x", (nz, ny, nx, M)), _ptr(params, "params", (4, nz, ny, nx)),
+        _ptr(lam, "lambda", (nz, ny, nx), allow_none=True), int(n_steps), float(beta_h), float(delta),
+        _ptr(F_out, "F_out", (nz, ny, nx, M), allow_none=True), C.c_void_p(workspace.data_ptr()),
+        workspace.numel(), _stream()))
+    return params
+
+
+class Study:
+    """Device-resident ICM state of one dynamic study (caller-owned tensors)."""
+
+    def __init__(self, geom: Geometry, kin: Kinetics, frame_dt, kappa, counts, x, params, F=None,
+                 randoms=None, bin_factor=None, params_given=False, n_lm=10, beta_kp=0.1,
+                 sigma2=1.0, beta_h=0.1, delta=0.01, workspace=None):
+        M = kin.M
+        dev = x.device
+        if F is None:
+            F = torch.zeros(geom.image_shape(M), device=dev, dtype=torch.float32)
+        if workspace is None:
+            workspace = _workspace(lib.kcs_study_workspace_size(geom.handle, M), dev)
+        pr, layout = _randoms(geom, randoms, M)
+        self._keep = (geom, kin, frame_dt, counts, x, params, F, randoms, bin_factor, workspace)
+        self.geom, self.kin, self.x, self.params, self.F = geom, kin, x, params, F
+        d = StudyDesc()
+        d.geom, d.kin, d.n_frames, d.kappa = geom.handle, kin.handle, M, float(kappa)
+        d.frame_dt = _ptr(frame_dt, "frame_dt", (M,))
+        d.counts = _ptr(counts, "counts", geom.sino_shape(M))
+        d.randoms, d.randoms_layout = pr, layout
+        d.bin_factor = _ptr(bin_factor, "bin_factor", (geom.nz, geom.n_angles, geom.n_bins),
+                            allow_none=True)
+        d.x = _ptr(x, "x", geom.image_shape(M))
+        d.params = _ptr(params, "params", (4, geom.nz, geom.ny, geom.nx))
+        d.F = _ptr(F, "F", geom.image_shape(M))
+        d.params_given, d.n_lm = int(bool(params_given)), int(n_lm)
+        d.beta_kp, d.sigma2, d.beta_h, d.delta = float(beta_kp), float(sigma2), float(beta_h), float(delta)
+        d.workspace, d.ws_bytes = C.c_void_p(workspace.data_ptr()), workspace.numel()
+        h = C.c_void_p()
+        check(lib.kcs_create_study(C.byref(h), C.byref(d)))
+        self.handle = h
+
+    def iterate(self, n_iter=1):
+        check(lib.kcs_icm_iterate(self.handle, int(n_iter), _stream()))
+
+    @property
+    def iterations(self):
+        return lib.kcs_study_iterations(self.handle)
+
+    def close(self):
+        if getattr(self, "handle", None):
+            lib.kcs_destroy_study(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        self.close()

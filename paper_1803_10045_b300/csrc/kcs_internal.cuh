@@ -1,0 +1,123 @@
+// Internal declarations of the kcs library (not part of the ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cstdint>
+#include <cstdio>
+#include <string>
+#include <vector>
+
+#include "../../include/kcs.h"
+
+namespace kcs {
+
+// ------------------------------------------------------------ errors
+void set_error(const char* fmt, ...);
+void clear_error();
+
+#define KCS_REQUIRE(cond, ...)                 \
+  do {                                         \
+    if (!(cond)) {                             \
+      ::kcs::set_error(__VA_ARGS__);           \
+      return KCS_ERR_INVALID_ARG;              \
+    }                                          \
+  } while (0)
+
+#define KCS_CUDA(call)                                                              \
+  do {                                                                              \
+    cudaError_t e_ = (call);                                                        \
+    if (e_ != cudaSuccess) {                                                        \
+      ::kcs::set_error("%s failed: %s (%s:%d)", #call, cudaGetErrorString(e_),      \
+                       __FILE__, __LINE__);                                         \
+      return e_ == cudaErrorMemoryAllocation ? KCS_ERR_OOM : KCS_ERR_CUDA;          \
+    }                                                                               \
+  } while (0)
+
+// A launch error (bad configuration) is reported without synchronising.
+#define KCS_LAUNCHED()                                                              \
+  do {                                                                              \
+    cudaError_t e_ = cudaGetLastError();                                            \
+    if (e_ != cudaSuccess) {                                                        \
+      ::kcs::set_error("kernel launch failed: %s (%s:%d)", cudaGetErrorString(e_),  \
+                       __FILE__, __LINE__);                                         \
+      return KCS_ERR_CUDA;                                                          \
+    }                                                                               \
+  } while (0)
+
+inline cudaStream_t as_stream(void* s) { return reinterpret_cast<cudaStream_t>(s); }
+
+// ------------------------------------------------------------ geometry
+// Per-angle Joseph constants.  Along the major axis (index t, centred
+// tf = t - (n_major-1)/2) the ray of bin b (centred bf = b - (B-1)/2) meets the
+// fractional minor index fr = fma(bf, beta, fma(tf, gamma, (n_minor-1)/2)).
+// x-major angles step over columns (minor = rows), the others over rows.
+struct AngleTab {
+  float beta;   // d fr / d bin
+  float gamma;  // d fr / d major step
+  float w;      // step weight h / max(|cos|, |sin|)
+  int xmajor;   // 1: major axis = columns
+};
+
+}  // namespace kcs
+
+struct kcs_geometry {
+  int nx, ny, nz, B, A, S;
+  float vox, bin;
+  int device;
+  kcs::AngleTab* d_ang;   // [A]
+  int* d_angles;          // subset lists concatenated, then 0..A-1 at offset A
+  std::vector<int> h_angles;
+  std::vector<int> off;   // off[k] .. off[k+1]: angles of subset k
+  int max_sub;
+};
+
+namespace kcs {
+
+inline int subset_count(const kcs_geometry* g, int k) {
+  return k < 0 ? g->A : g->off[k + 1] - g->off[k];
+}
+inline const int* subset_dev(const kcs_geometry* g, int k) {
+  return k < 0 ? g->d_angles + g->A : g->d_angles + g->off[k];
+}
+inline size_t align256(size_t n) { return (n + 255) & ~size_t(255); }
+
+// ------------------------------------------------------------ kinetics
+constexpr int KMAX = 64;        // series terms per interval (max)
+constexpr int NCH = 12;         // channels per term, padded to 3 float4
+constexpr double DT_MAX = 5.0;  // longest propagation interval (min)
+
+// Channel order inside a term's 12 floats.
+enum { CH_M1 = 0, CH_G, CH_M2, CH_H, CH_M3, CH_D1, CH_GP, CH_D2, CH_HP, CH_D3 };
+
+struct KinDev {
+  const float4* coef;   // [n_iv][KMAX][3] float4 (12 channels)
+  const float* iv_dt;   // [n_iv] interval length (min)
+  const int* iv_code;   // [n_iv]: -1 gap, else 2*frame + (last piece of the frame)
+  const float* fr_cp;   // [M] frame average of Cp
+  const float* fr_inv;  // [M] 1 / frame duration
+  int n_iv;
+  int M;
+};
+
+}  // namespace kcs
+
+struct kcs_kinetics {
+  int M;
+  int n_iv;
+  int device;
+  float4* d_coef;
+  float* d_iv_dt;
+  int* d_iv_code;
+  float* d_fr_cp;
+  float* d_fr_inv;
+  double* d_tmp;  // per-interval doubles used while tabulating
+  kcs::KinDev dev() const {
+    return kcs::KinDev{d_coef, d_iv_dt, d_iv_code, d_fr_cp, d_fr_inv, n_iv, M};
+  }
+};
+
+namespace kcs {
+// launchers shared between translation units
+int launch_tac_eval(const kcs_kinetics* k, int64_t n_vox, const float* params, float* F,
+                    float* J, cudaStream_t s);
+}  // namespace kcs
