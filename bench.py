@@ -1,0 +1,365 @@
+#!/usr/bin/env python
+"""ICM throughput on the full-size stacked-2D workload (one JSON line).
+
+Workload (config PR2): 344 x 344 x 127 voxels of 2.09 mm, 24 frames (8x15 s,
+4x60 s, 6x180 s, 6x300 s), 344 bins x 252 angles, 21 subsets, brain-like
+phantom with 20 lesions and 10 % parameter jitter, ~2e8 prompts (80 % trues,
+20 % uniform randoms), 10 MAP-LM steps per ICM iteration.  A step is one ICM
+iteration: 21 x (forward projection + ratio, back-projection + OSL update),
+10 MAP-LM steps and the model TACs for the next prior.  Inputs are synthetic
+(the paper's human data are not available) and resident in HBM; the image
+series (1.44 GB) and the counts (1.06 GB) are larger than the 126 MB L2.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+--impl reference times the FP64 CPU oracle on a bounded sample of the same
+workload (one plane, one subset update, one LM step on 4096 voxels) and
+extrapolates to ICM iter/s; it is a deliberately slow, untuned baseline.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import kcs_synth as S  # noqa: E402
+
+METRIC = "ICM iter/s at 344²×127×24 frames"
+WORKLOAD = "PR2: 344x344x127 (2.09 mm), 344 bins x 252 angles, 24 frames, 21 subsets, 10 LM steps/iter"
+N_LM = 10
+BETA_KP, BETA_H, DELTA = 0.1, 0.1, 0.01
+FP32_LANES_PER_SM, N_SM = 128, 148
+# Nominal float32 FLOPs of one MAP-LM voxel-step on this workload: 15 Horner
+# channels x 2 flop x (sum over the 24 intervals of K = 12 + ceil(2.72 a D) at
+# a = 0.19: 330 terms), 24 frames x (2 x 25 recursion + 2 x 15 normal-equation)
+# flop, and ~400 flop of Huber terms and step logic.
+LM_FLOPS_PER_VOXEL_STEP = 2 * 15 * 330 + 24 * (2 * 25 + 2 * 15) + 400
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            p = json.load(f)
+        return p.get("hbm_gbs", 6400.0), p.get("sm_max_mhz", 2032.0), "measured"
+    except OSError:
+        return 6400.0, 2032.0, "fallback"
+
+
+# ------------------------------------------------------------------ clocks
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons while running."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except OSError:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.thread.join(timeout=2)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                smax.append(float(parts[1]))
+            except ValueError:
+                continue
+            for n, v in zip(names, parts[4:8]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ------------------------------------------------------------------ CPU oracle sample
+def oracle_sample(reps=1, seed=0):
+    """Time the FP64 oracle on a bounded sample of the PR2 workload and
+    extrapolate to ICM iterations per second (1 thread)."""
+    from threadpoolctl import threadpool_limits
+
+    from oracle import lm as OL
+    from oracle import osl as OO
+    from oracle import projector as OP
+    W = S.WORKLOADS["pr2"]
+    ts, te = W.frames()
+    dt = te - ts
+    M = W.n_frames
+    og = OP.Geometry(W.nx, W.ny, W.vox_mm, W.n_bins, W.n_angles, W.bin_mm, W.n_subsets)
+    k = 5
+    x = S.random_images((1, W.ny, W.nx, M), seed=seed, lo=1.0, hi=20.0)
+    counts_k = S.poisson(np.full((1, len(og.subsets[k]), W.n_bins, M), 5.0), seed)
+    F = 0.9 * x
+    nvox = 4096
+    lm_x = x.reshape(-1, M)[:nvox].reshape(1, 64, 64, M)
+    lm_maps = np.broadcast_to(np.array(S.XI0)[:, None, None, None], (4, 1, 64, 64)).copy()
+    lam = np.full((1, 64, 64), 1e-2)
+    t_osl, t_lm = [], []
+    with threadpool_limits(limits=1):
+        og.P(k)                                    # system matrix of the subset (setup)
+        for _ in range(reps):
+            t0 = time.perf_counter()
+            OO.osl_update(og, x, k, counts_k, 1.0, dt, F=F, beta=BETA_KP)
+            t1 = time.perf_counter()
+            OL.lm_step(lm_x, lm_maps, lam, ts, te, S.FENG, BETA_H, DELTA)
+            t2 = time.perf_counter()
+            t_osl.append(t1 - t0)
+            t_lm.append(t2 - t1)
+    to, tl = min(t_osl), min(t_lm)
+    V_plane = W.nx * W.ny
+    t_iter = W.nz * (W.n_subsets * to + N_LM * tl * V_plane / nvox)
+    return {"value": 1.0 / t_iter, "unit": "iter/s", "cores": 1, "kind": "oracle",
+            "sample": (f"one plane: one subset OSL update ({to:.3f} s) and one MAP-LM step on "
+                       f"{nvox} voxels ({tl:.3f} s), FP64 numpy, 1 thread; extrapolated to "
+                       f"{W.nz} planes x ({W.n_subsets} subsets + {N_LM} LM steps over "
+                       f"{V_plane} voxels) = {t_iter:.0f} s per ICM iteration")}
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    for _ in range(args.warmup):
+        oracle_sample()
+    t0 = time.perf_counter()
+    vals = [oracle_sample() for _ in range(args.steps)]
+    wall = time.perf_counter() - t0
+    v = statistics.median(r["value"] for r in vals)
+    cb = dict(vals[0])
+    cb["value"] = v
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": v, "unit": "iter/s",
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1000.0 / v, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "sample_wall_s": round(wall, 2)},
+        "cpu_baseline": cb,
+        "e2e": {"value": v, "unit": "iter/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}))
+
+
+# ------------------------------------------------------------------ GPU arm
+def build_problem(K, torch, dev, seed=0):
+    """Synthetic PR2 study on the device: true maps -> model TACs -> projection
+    -> Poisson counts (80 % trues, 20 % uniform randoms)."""
+    W = S.WORKLOADS["pr2"]
+    ts, te = W.frames()
+    g = K.Geometry(W.nx, W.ny, W.nz, W.vox_mm, W.n_bins, W.n_angles, W.bin_mm, W.n_subsets)
+    kin = K.Kinetics(ts, te, S.FENG)
+    dt = torch.tensor(te - ts, dtype=torch.float32, device=dev)
+    xi = torch.from_numpy(S.phantom_pr2(W.nx, W.nz, seed=seed)).to(dev)
+    Ft = K.tac_eval(kin, xi)
+    ybar = K.forward_project(g, Ft)
+    del Ft, xi
+    ybar.mul_(dt)
+    trues = W.total_prompts * (1 - W.randoms_frac)
+    kappa = float(trues / ybar.double().sum().item())
+    n_bins_total = W.nz * W.n_angles * W.n_bins
+    r = (W.total_prompts * W.randoms_frac) * dt / (dt.sum() * n_bins_total)
+    ybar.mul_(kappa).add_(r)
+    gen = torch.Generator(device=dev).manual_seed(seed)
+    counts = torch.poisson(ybar, generator=gen)
+    del ybar
+    return W, g, kin, dt, kappa, counts, r.contiguous()
+
+
+def run_ours(args):
+    import torch
+
+    import paper_1803_10045_b300 as K
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    W, g, kin, dt, kappa, counts, r = build_problem(K, torch, dev, seed=rank)
+    M = W.n_frames
+    x = K.init_image(g, dt, kappa, counts, r)
+    params = torch.empty((4, W.nz, W.ny, W.nx), device=dev)
+    params[:] = torch.tensor(S.XI0, device=dev)[:, None, None, None]
+    F = torch.zeros_like(x)
+    st = K.Study(g, kin, dt, kappa, counts, x, params, F=F, randoms=r, n_lm=N_LM,
+                 beta_kp=BETA_KP, beta_h=BETA_H, delta=DELTA)
+    for _ in range(args.warmup):
+        st.iterate(1)
+    torch.cuda.synchronize()
+
+    # ---- timed region: the kernels icm_iterate issues, with events between them
+    S_ = W.n_subsets
+    rhos = {g.n_sub(k): torch.empty(g.sino_shape(M, k), device=dev) for k in range(S_)}
+    lm_ws = torch.empty(K.lm_workspace_size(W.nx, W.ny, W.nz), dtype=torch.uint8, device=dev)
+
+    def ev():
+        e = torch.cuda.Event(enable_timing=True)
+        e.record()
+        return e
+
+    def step(marks):
+        for k in range(S_):
+            rk = rhos[g.n_sub(k)]
+            K.osl_ratio(g, k, x, dt, kappa, counts, r, out=rk)
+            marks.append(("fwd_ratio", ev()))
+            K.osl_backproject(g, k, x, dt, kappa, rk, F=F, beta=BETA_KP)
+            marks.append(("bwd_osl", ev()))
+        K.map_lm_fit(kin, x, params, N_LM, BETA_H, DELTA, workspace=lm_ws)
+        marks.append(("lm_step", ev()))
+        K.tac_eval(kin, params, out=F)
+        marks.append(("tac_eval", ev()))
+
+    sampler = ClockSampler(local)
+    sampler.start()
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    marks = [("start", ev())]
+    for _ in range(args.steps):
+        step(marks)
+    end = marks[-1][1]
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    clocks = sampler.stop()
+    total_ms = marks[0][1].elapsed_time(end)
+    if dist:
+        t = torch.tensor([total_ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = t.item()
+    per = {}
+    for (_, a), (name, b) in zip(marks[:-1], marks[1:]):
+        per.setdefault(name, []).append(a.elapsed_time(b))
+    ok = bool(torch.isfinite(params).all().item() and torch.isfinite(x).all().item())
+
+    # ---- end to end through the public API with host buffers
+    counts_h = torch.empty(counts.shape, dtype=torch.float32, pin_memory=True)
+    counts_h.copy_(counts)
+    params_h = torch.empty(params.shape, dtype=torch.float32, pin_memory=True)
+    torch.cuda.synchronize()
+    e0 = ev()
+    for _ in range(args.steps):
+        counts.copy_(counts_h, non_blocking=True)
+        st.iterate(1)
+        params_h.copy_(params, non_blocking=True)
+    e1 = ev()
+    torch.cuda.synchronize()
+    e2e_ms = e0.elapsed_time(e1)
+
+    if rank != 0:
+        if dist:
+            dist.destroy_process_group()
+        return
+    value = world * args.steps / (total_ms / 1e3)
+    hbm, smax, src = _peaks()
+    V = W.nx * W.ny * W.nz
+    img = V * M * 4
+    n_sub = W.n_angles // W.n_subsets
+    sino_k = W.nz * n_sub * W.n_bins * M * 4
+    alg = {  # algorithmic bytes per launch
+        "fwd_ratio": img + 2 * sino_k,            # read x, counts_k; write rho
+        "bwd_osl": sino_k + 3 * img,              # read rho, x, F; write x
+        "lm_step": img + 2 * 4 * V * 4 + 2 * V * 4,   # x; params in/out; lambda in/out
+        "tac_eval": 4 * V * 4 + img,
+    }
+    n_launch = {"fwd_ratio": S_, "bwd_osl": S_, "lm_step": N_LM, "tac_eval": 1}
+    kernels = {}
+    for name, ts_ in per.items():
+        launches = n_launch[name] * args.steps
+        avg = sum(ts_) / launches
+        kernels[name] = {"launches": launches, "avg_ms": round(avg, 4),
+                         "share": round(sum(ts_) / total_ms, 4),
+                         "alg_GBps": round(alg[name] / (avg * 1e-3) / 1e9, 1)}
+    dom = max(kernels, key=lambda n: kernels[n]["share"])
+    fp32_peak = N_SM * FP32_LANES_PER_SM * 2 * smax * 1e6 / 1e12
+    if dom == "lm_step":
+        ach = V * LM_FLOPS_PER_VOXEL_STEP / (kernels[dom]["avg_ms"] * 1e-3) / 1e12
+        roof = {"bound": "alu", "kernel": dom, "achieved": round(ach, 2),
+                "peak": round(fp32_peak, 1), "unit": "TFLOP/s", "frac": round(ach / fp32_peak, 4),
+                "traffic": None,
+                "peak_source": f"FP32 FMA {N_SM} SM x {FP32_LANES_PER_SM} lanes x 2 x {smax:.0f} MHz"}
+    else:
+        ach = kernels[dom]["alg_GBps"]
+        roof = {"bound": "hbm", "kernel": dom, "achieved": ach, "peak": hbm, "unit": "GB/s",
+                "frac": round(ach / hbm, 4), "traffic": None, "peak_source": f"{src} hbm_gbs"}
+    lm_ms = kernels["lm_step"]["avg_ms"]
+    out = {
+        "metric": METRIC, "value": round(value, 4), "unit": "iter/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(total_ms / args.steps, 3),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic",
+        "config": {"workload": WORKLOAD, "voxels": V, "frames": M, "subsets": S_, "lm_steps": N_LM,
+                   "l2": "inputs larger than L2 (image series 1.44 GB, counts 1.06 GB)",
+                   "randoms": "uniform per frame"},
+        "roofline": roof,
+        "kernels": kernels,
+        "voxel_lm_fits_per_s": round(V / (N_LM * lm_ms * 1e-3), 1),
+        "voxel_lm_steps_per_s": round(V / (lm_ms * 1e-3), 1),
+        "gpu_launches": args.steps * (2 * S_ + N_LM + 1),
+        "clocks": clocks,
+        "e2e": {"value": round(world * args.steps / (e2e_ms / 1e3), 4), "unit": "iter/s",
+                "h2d_bytes_per_step": counts.numel() * 4, "d2h_bytes_per_step": params.numel() * 4},
+        "finite": ok,
+    }
+    if not args.no_cpu_baseline:
+        out["cpu_baseline"] = oracle_sample()
+    print(json.dumps(out))
+    if dist:
+        dist.destroy_process_group()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

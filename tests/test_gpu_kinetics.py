@@ -1,0 +1,74 @@
+"""CUDA frame-integrated 2TC model (F and Jacobian) vs the FP64 oracle (GPU).
+
+Tolerance derivation: the kernel sums positive series by Horner in float32
+(relative error <= K eps, K <= 64 terms) and propagates two running integrals
+over <= 40 intervals, so F carries a relative error of a few 1e-6; the k3
+column of J subtracts two such terms, so J is compared with an absolute error
+relative to its column's largest entry.
+"""
+import numpy as np
+import pytest
+import torch
+
+import kcs_synth as S
+from oracle import kinetics as OK
+
+pytestmark = pytest.mark.gpu
+
+L3, L2 = S.FENG["l3"], S.FENG["l2"]
+EDGE = np.array([
+    [0.10, 0.13, 0.06, 0.04],      # GM
+    [0.05, 0.10, 0.04, 0.03],      # WM
+    [0.03, 0.08, 0.02, 0.02],      # background
+    [0.30, 0.0, 0.0, 0.05],        # a = 0
+    [0.30, 1e-7, 1e-7, 0.05],      # a -> 0
+    [0.20, L3 - 0.05, 0.05, 0.1],  # a = l3
+    [0.20, L2, 0.0, 0.1],          # a = l2
+    [2.0, 2.0, 1.0, 0.0],          # upper corner of the LM box
+    [0.0, 0.5, 0.5, 0.3],          # K1 = 0
+    [0.4, 0.2, 0.1, 1.0],          # pure blood
+    [1.0, 0.01, 0.99, 0.5],
+])
+
+SCHEDS = {
+    "pr1": S.schedule(S.SCHEDULES["pr1"]),
+    "pr2": S.schedule(S.SCHEDULES["pr2"]),
+    "paper": S.schedule(S.SCHEDULES["paper"]),          # 600 s frame: split on the device
+    "gaps": (np.array([0.5, 1.0, 4.0, 10.0]), np.array([0.75, 2.0, 7.0, 12.5])),
+}
+
+
+def _check(ts, te, xi):
+    import paper_1803_10045_b300 as K
+    kin = K.Kinetics(ts, te, S.FENG)
+    p = torch.tensor(xi.T.copy(), dtype=torch.float32, device="cuda")
+    F, J = K.tac_eval(kin, p, jacobian=True)
+    F = F.double().cpu().numpy()
+    J = J.double().cpu().numpy()
+    # the oracle sees the parameters the GPU saw (float32-rounded)
+    Fr, Jr = OK.model(xi.astype(np.float32).astype(np.float64), ts, te, S.FENG)
+    scale = np.maximum(np.abs(Fr), 1e-3 * np.abs(Fr).max())
+    assert np.max(np.abs(F - Fr) / scale) < 1e-5
+    for q in range(4):
+        col = np.abs(Jr[:, :, q]).max(axis=1, keepdims=True) + 1e-12
+        assert np.max(np.abs(J[:, :, q] - Jr[:, :, q]) / col) < 1e-4, q
+
+
+@pytest.mark.parametrize("sched", list(SCHEDS))
+def test_model_edge_cases(cuda_ok, sched):
+    ts, te = SCHEDS[sched]
+    _check(ts, te, EDGE)
+
+
+@pytest.mark.parametrize("sched", ["pr1", "pr2"])
+def test_model_jittered(cuda_ok, sched):
+    ts, te = SCHEDS[sched]
+    xi = np.clip(S.jittered_params(3000, seed=9, rel=0.9), 0, [2, 2, 1, 1])
+    _check(ts, te, xi)
+
+
+def test_ki(cuda_ok):
+    import paper_1803_10045_b300 as K
+    p = torch.tensor(EDGE.T.copy(), dtype=torch.float32, device="cuda")
+    got = K.ki(p).double().cpu().numpy()
+    np.testing.assert_allclose(got, OK.ki(EDGE.T.astype(np.float32).astype(np.float64)), rtol=1e-6)

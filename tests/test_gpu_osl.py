@@ -1,0 +1,95 @@
+"""CUDA OS-MAP-OSL-KP update vs the FP64 oracle, teacher-forced (GPU).
+
+Both sides start every update from the same image; the GPU result must be
+within 1e-4 relative L2 of the oracle's (the image tolerance of the method).
+"""
+import numpy as np
+import pytest
+import torch
+
+from oracle import osl as OO
+from oracle import projector as OP
+from cases import pr1_problem, rel_l2
+
+pytestmark = pytest.mark.gpu
+
+
+def _t(a):
+    return torch.tensor(np.ascontiguousarray(a), dtype=torch.float32, device="cuda")
+
+
+def _f32(a):
+    return None if a is None else np.asarray(a, np.float32).astype(np.float64)
+
+
+def _small(seed=0, randoms="full", nf=True):
+    nx, ny, nz, B, A, Sb, M = 37, 31, 2, 47, 36, 4, 8
+    og = OP.Geometry(nx, ny, 2.0, B, A, 2.0, Sb)
+    rng = np.random.default_rng(seed)
+    x_true = rng.uniform(0.5, 3.0, (nz, ny, nx, M))
+    dt = np.linspace(0.25, 3.0, M)
+    kappa = 3.0
+    n = rng.uniform(0.7, 1.3, (nz, A, B)) if nf else None
+    ybar = og.forward(x_true) * kappa * dt * (n[..., None] if nf else 1.0)
+    r = None
+    if randoms == "full":
+        r = rng.uniform(0.1, 0.5, ybar.shape) * ybar.mean()
+    elif randoms == "frame":
+        r = np.full(M, 0.2 * ybar.mean())
+    counts = rng.poisson(ybar + (0 if r is None else r)).astype(float)
+    x0 = rng.uniform(0.5, 3.0, x_true.shape)
+    F = x_true * rng.uniform(0.8, 1.2, x_true.shape)
+    # both sides consume float32-representable inputs
+    return og, (nx, ny, nz, B, A, Sb, M), _f32(x0), _f32(dt), kappa, counts, _f32(r), _f32(n), _f32(F)
+
+
+@pytest.mark.parametrize("randoms", ["none", "frame", "full"])
+@pytest.mark.parametrize("prior", [0.0, 2.0])
+def test_osl_update_matches_oracle(cuda_ok, randoms, prior):
+    import paper_1803_10045_b300 as K
+    og, (nx, ny, nz, B, A, Sb, M), x0, dt, kappa, counts, r, n, F = _small(randoms=randoms)
+    kg = K.Geometry(nx, ny, nz, 2.0, B, A, 2.0, Sb)
+    rfull = None if r is None else (np.broadcast_to(r, counts.shape) if r.ndim == 1 else r)
+    for k in range(Sb):
+        xg = _t(x0)
+        K.osl_update(kg, k, xg, _t(dt), kappa, _t(counts), None if r is None else _t(r), _t(n),
+                     _t(F) if prior else None, prior, 1.0)
+        ref = OO.osl_update(og, x0, k, counts[:, og.subsets[k]], kappa, dt, n[:, og.subsets[k]],
+                            None if rfull is None else rfull[:, og.subsets[k]],
+                            F if prior else None, prior, 1.0)
+        assert rel_l2(xg.cpu().numpy(), ref) < 1e-4
+
+
+def test_sensitivity_matches_oracle(cuda_ok):
+    import paper_1803_10045_b300 as K
+    og, (nx, ny, nz, B, A, Sb, M), x0, dt, kappa, counts, r, n, F = _small()
+    kg = K.Geometry(nx, ny, nz, 2.0, B, A, 2.0, Sb)
+    s = K.sensitivity(kg, 2, _t(n)).cpu().numpy()
+    ref = og.back(n[:, og.subsets[2], :, None], 2)[..., 0]
+    assert rel_l2(s, ref) < 1e-5
+
+
+def test_init_image_matches_oracle(cuda_ok):
+    import paper_1803_10045_b300 as K
+    og, (nx, ny, nz, B, A, Sb, M), x0, dt, kappa, counts, r, n, F = _small(randoms="full")
+    kg = K.Geometry(nx, ny, nz, 2.0, B, A, 2.0, Sb)
+    x = K.init_image(kg, _t(dt), kappa, _t(counts), _t(r), _t(n)).cpu().numpy()
+    ref = OO.initial_image(og, counts, kappa, dt, nz, n, r)
+    np.testing.assert_allclose(x, ref, rtol=1e-5)
+
+
+def test_pr1_osem_pass_matches_oracle(cuda_ok):
+    # Config PR1 data, one full pass over the 4 subsets from the uniform start image.
+    import paper_1803_10045_b300 as K
+    P = pr1_problem()
+    W = P["W"]
+    kg = K.Geometry(W.nx, W.ny, W.nz, W.vox_mm, W.n_bins, W.n_angles, W.bin_mm, W.n_subsets)
+    x0 = _f32(OO.initial_image(P["g"], P["counts"], P["kappa"], P["dt"], 1))
+    dt = _f32(P["dt"])
+    xg = _t(x0)
+    ct, dtt = _t(P["counts"]), _t(dt)
+    x = x0.copy()
+    for k in range(W.n_subsets):
+        K.osl_update(kg, k, xg, dtt, P["kappa"], ct)
+        x = OO.osl_update(P["g"], x, k, P["counts"][:, P["g"].subsets[k]], P["kappa"], dt)
+    assert rel_l2(xg.cpu().numpy(), x) < 1e-4
