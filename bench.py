@@ -113,10 +113,18 @@ class ClockSampler:
 
 # ------------------------------------------------------------------ CPU oracle sample
 def oracle_sample(reps=1, seed=0):
-    """Time the FP64 oracle on a bounded sample of the PR2 workload and
-    extrapolate to ICM iterations per second (1 thread)."""
-    from threadpoolctl import threadpool_limits
+    """Time the FP64 oracle on a bounded sample of the PR2 workload in a fresh
+    single-threaded process and extrapolate to ICM iterations per second."""
+    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1",
+               CUDA_VISIBLE_DEVICES="")
+    code = (f"import json, sys; sys.path.insert(0, {ROOT!r}); import bench; "
+            f"print(json.dumps(bench._oracle_sample_inner({reps}, {seed})))")
+    out = subprocess.run([sys.executable, "-c", code], env=env, capture_output=True, text=True,
+                         check=True)
+    return json.loads(out.stdout.strip().splitlines()[-1])
 
+
+def _oracle_sample_inner(reps=1, seed=0):
     from oracle import lm as OL
     from oracle import osl as OO
     from oracle import projector as OP
@@ -134,16 +142,15 @@ def oracle_sample(reps=1, seed=0):
     lm_maps = np.broadcast_to(np.array(S.XI0)[:, None, None, None], (4, 1, 64, 64)).copy()
     lam = np.full((1, 64, 64), 1e-2)
     t_osl, t_lm = [], []
-    with threadpool_limits(limits=1):
-        og.P(k)                                    # system matrix of the subset (setup)
-        for _ in range(reps):
-            t0 = time.perf_counter()
-            OO.osl_update(og, x, k, counts_k, 1.0, dt, F=F, beta=BETA_KP)
-            t1 = time.perf_counter()
-            OL.lm_step(lm_x, lm_maps, lam, ts, te, S.FENG, BETA_H, DELTA)
-            t2 = time.perf_counter()
-            t_osl.append(t1 - t0)
-            t_lm.append(t2 - t1)
+    og.P(k)                                    # system matrix of the subset (setup)
+    for _ in range(reps):
+        t0 = time.perf_counter()
+        OO.osl_update(og, x, k, counts_k, 1.0, dt, F=F, beta=BETA_KP)
+        t1 = time.perf_counter()
+        OL.lm_step(lm_x, lm_maps, lam, ts, te, S.FENG, BETA_H, DELTA)
+        t2 = time.perf_counter()
+        t_osl.append(t1 - t0)
+        t_lm.append(t2 - t1)
     to, tl = min(t_osl), min(t_lm)
     V_plane = W.nx * W.ny
     t_iter = W.nz * (W.n_subsets * to + N_LM * tl * V_plane / nvox)

@@ -163,8 +163,8 @@ int kcs_huber_grad(int nx, int ny, int nz, const float* params, float delta, flo
 /* n_steps synchronous MAP-LM steps (Eq. 4) of every voxel's TAC x [Z][ny][nx][M]:
  *   (J^T J + lambda I) step = J^T (x - F) - beta_h dH/dxi      (solved in float64)
  *   trial = clamp(xi + step, 0, (2, 2, 1, 1)); accept iff the voxel objective
- *   1/2 |x - F|^2 + beta_h sum_p sum_{N8} huber(xi_p - xi_{k,p}) decreases,
- *   with the neighbours frozen at their start-of-step values;
+ *   Phi = 1/2 |x - F|^2 + beta_h sum_p sum_{N8} huber(xi_p - xi_{k,p}) falls by
+ *   more than 1e-5 Phi, with the neighbours frozen at their start-of-step values;
  *   lambda /= 10 (>= 1e-7) on accept, *= 10 (<= 1e7) on reject.
  * params [4][Z][ny][nx] in/out; lambda [Z][ny][nx] in/out, or NULL to start
  * every voxel at 1e-2; F_out [Z][ny][nx][M] receives F(final params) when not

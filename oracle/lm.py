@@ -23,12 +23,16 @@ MAP-LM step for voxel v with neighbours frozen at their start-of-step values
     Phi_v(xi) = 1/2 |x_v - F(xi)|^2 + beta H_v(xi)
     (J^T J + lambda I) step = J^T (x_v - F(xi)) - beta dH_v/dxi      (Eq. 4)
     trial = clamp(xi + step, lo, hi)
-    accept iff Phi_v(trial) < Phi_v(xi):  lambda <- max(lambda/10, 1e-7)
-    else keep xi:                          lambda <- min(10 lambda, 1e7)
+    accept iff Phi_v(trial) - Phi_v(xi) < -tau Phi_v(xi):  lambda <- max(lambda/10, 1e-7)
+    else keep xi:                                           lambda <- min(10 lambda, 1e7)
 
 Readings: Levenberg damping lambda I exactly as printed (not Marquardt's
 diagonal); the box [lo, hi] keeps the trial physical (the paper names none);
-lambda starts at 1e-2 on every fit call; equal objectives count as reject.
+lambda starts at 1e-2 on every fit call.  The paper states no acceptance rule;
+a trial must lower the voxel objective by more than tau = 1e-5 of its value,
+because smaller changes are below what a float32 evaluation of the model can
+resolve (they are rounding noise, and a float32 and a float64 implementation
+would otherwise decide them differently); equal objectives count as reject.
 
 Pins (tests/test_oracle_lm.py): noise-free recovery with beta = 0, a brute
 force parameter grid on single voxels, delta -> infinity giving the quadratic
@@ -43,6 +47,7 @@ from . import kinetics
 
 LAMBDA0 = 1e-2
 LAMBDA_MIN, LAMBDA_MAX = 1e-7, 1e7
+TAU = 1e-5          # relative objective decrease required to accept a trial
 NEIGHBOURS = [(dy, dx) for dy in (-1, 0, 1) for dx in (-1, 0, 1) if (dy, dx) != (0, 0)]
 
 
@@ -111,7 +116,7 @@ def lm_step(x, maps, lam, t_start, t_end, feng, beta, delta,
     rt = xv - Ft
     trial_maps = trial.T.reshape(maps.shape)
     phi_t = 0.5 * np.sum(rt * rt, axis=1) + beta * huber_local(trial_maps, maps, delta).ravel()
-    acc = phi_t < phi
+    acc = (phi_t - phi) < -TAU * phi
     new = np.where(acc[:, None], trial, xi)
     lam_new = np.where(acc, np.maximum(lam.ravel() / 10, LAMBDA_MIN),
                        np.minimum(lam.ravel() * 10, LAMBDA_MAX))

@@ -154,20 +154,24 @@ __device__ __forceinline__ void eval_model(const KinDev& kd, float K1, float k2,
     const float G = E * p_g, H = E * p_h;
     const float A = fmaf(I, G, E * p_m2);
     const float B = fmaf(Jr, D, fmaf(I, H, E * p_m3));
+    const int code = __ldg(kd.iv_code + iv);
     if (JAC) {
       const float Gp = -E * p_gp, Hp = -E * p_hp;
       const float Ap = fmaf(Ip, G, fmaf(I, Gp, -E * p_d2));
       const float Bp = fmaf(Jp, D, fmaf(Ip, H, fmaf(I, Hp, -E * p_d3)));
       Ip = fmaf(E, fmaf(-D, I, Ip), -E * p_d1);
       Jp += Ap;
-      SAp += Ap;
-      SBp += Bp;
+      if (code >= 0) {   // gaps between frames propagate the state only
+        SAp += Ap;
+        SBp += Bp;
+      }
     }
     I = fmaf(E, I, E * p_m1);
     Jr += A;
-    SA += A;
-    SB += B;
-    const int code = __ldg(kd.iv_code + iv);
+    if (code >= 0) {
+      SA += A;
+      SB += B;
+    }
     if (code >= 0 && (code & 1)) {
       const int m = code >> 1;
       const float inv = __ldg(kd.fr_inv + m);
@@ -176,9 +180,13 @@ __device__ __forceinline__ void eval_model(const KinDev& kd, float K1, float k2,
       const float T = K1 * S;
       const float F = fmaf(Vb, cp - T, T);      // (1 - Vb) T + Vb cp
       if (JAC) {
+        // dC_T/dk2 = K1 (dI/da + k3 dJ/da); dC_T/dk3 = K1 (dI/da + J + k3 dJ/da),
+        // and dI/da + J = -a dJ/da (from I' = Cp - a I), so dC_T/dk3 = -K1 k2 dJ/da:
+        // a single non-negative term, exactly 0 at k2 = 0 instead of a cancelling
+        // difference.
         const float w = 1.f - Vb;
         const float Sp = fmaf(k3, SBp, SAp) * inv;
-        sink(m, F, w * S, w * K1 * Sp, w * K1 * fmaf(SB, inv, Sp), cp - T);
+        sink(m, F, w * S, w * K1 * Sp, -w * K1 * k2 * SBp * inv, cp - T);
       } else {
         sink(m, F, 0.f, 0.f, 0.f, 0.f);
       }
@@ -293,6 +301,9 @@ constexpr int LM_THREADS = 128;
 __constant__ float c_lo[4] = {0.f, 0.f, 0.f, 0.f};
 __constant__ float c_hi[4] = {2.f, 2.f, 1.f, 1.f};
 constexpr float LAMBDA0 = 1e-2f, LAMBDA_MIN = 1e-7f, LAMBDA_MAX = 1e7f;
+// A trial is accepted when it lowers the voxel objective by more than TAU of its
+// value: smaller changes are below float32 resolution of the model.
+constexpr float TAU = 1e-5f;
 
 struct LmArgs {
   KinDev kd;
@@ -307,12 +318,14 @@ struct LmArgs {
 
 struct NormalSink {
   const float* xs;   // this voxel's TAC in shared memory
-  float phi;
+  float* fc;         // this voxel's model TAC at the current point (shared memory)
+  float rr;          // sum of squared residuals at the current point
   float A00, A01, A02, A03, A11, A12, A13, A22, A23, A33;
   float b0, b1, b2, b3;
   __device__ void operator()(int m, float F, float j0, float j1, float j2, float j3) {
     const float r = xs[m] - F;
-    phi = fmaf(r, r, phi);
+    fc[m] = F;
+    rr = fmaf(r, r, rr);
     A00 = fmaf(j0, j0, A00); A01 = fmaf(j0, j1, A01); A02 = fmaf(j0, j2, A02); A03 = fmaf(j0, j3, A03);
     A11 = fmaf(j1, j1, A11); A12 = fmaf(j1, j2, A12); A13 = fmaf(j1, j3, A13);
     A22 = fmaf(j2, j2, A22); A23 = fmaf(j2, j3, A23);
@@ -321,12 +334,17 @@ struct NormalSink {
   }
 };
 
-struct ResidualSink {
+// Change of the data term between the current point (fc) and the trial,
+// 1/2 sum (x - F')^2 - 1/2 sum (x - F)^2 = sum (F - F') (x - (F + F')/2),
+// accumulated directly so that small decreases are not lost in the rounding of
+// two large sums.
+struct DeltaSink {
   const float* xs;
-  float phi;
+  const float* fc;
+  float dphi;
   __device__ void operator()(int m, float F, float, float, float, float) {
-    const float r = xs[m] - F;
-    phi = fmaf(r, r, phi);
+    const float Fc = fc[m];
+    dphi = fmaf(Fc - F, xs[m] - 0.5f * (Fc + F), dphi);
   }
 };
 
@@ -365,6 +383,7 @@ __global__ void __launch_bounds__(LM_THREADS) k_lm_step(LmArgs L) {
   extern __shared__ float xs_all[];
   const int M = L.kd.M;
   const int ld = M + 1;
+  float* fc_all = xs_all + LM_THREADS * ld;
   const long long V = (long long)L.nx * L.ny * L.nz;
   const long long v0 = (long long)blockIdx.x * LM_THREADS;
   const long long v = v0 + threadIdx.x;
@@ -395,9 +414,9 @@ __global__ void __launch_bounds__(LM_THREADS) k_lm_step(LmArgs L) {
         Hc += huber_h(t, L.delta);
       }
     }
-  NormalSink ns{xs, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+  float* fc = fc_all + threadIdx.x * ld;
+  NormalSink ns{xs, fc, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
   eval_model<true>(L.kd, xi[0], xi[1], xi[2], xi[3], ns);
-  const float phi = fmaf(0.5f, ns.phi, L.beta * Hc);
   float lam = L.reset_lambda ? LAMBDA0 : L.lambda[v];
   const double rhs[4] = {(double)ns.b0 - (double)L.beta * g[0], (double)ns.b1 - (double)L.beta * g[1],
                          (double)ns.b2 - (double)L.beta * g[2], (double)ns.b3 - (double)L.beta * g[3]};
@@ -406,19 +425,23 @@ __global__ void __launch_bounds__(LM_THREADS) k_lm_step(LmArgs L) {
   float tr[4];
   if (solve4(ns, (double)lam, rhs, step)) {
     for (int q = 0; q < 4; ++q) tr[q] = fminf(fmaxf(xi[q] + (float)step[q], c_lo[q]), c_hi[q]);
-    ResidualSink rs{xs, 0.f};
-    eval_model<false>(L.kd, tr[0], tr[1], tr[2], tr[3], rs);
-    float Ht = 0.f;
+    DeltaSink ds{xs, fc, 0.f};
+    eval_model<false>(L.kd, tr[0], tr[1], tr[2], tr[3], ds);
+    float dH = 0.f;   // H(trial) - H(current), neighbours frozen
     for (int dy = -1; dy <= 1; ++dy)
       for (int dx = -1; dx <= 1; ++dx) {
         if (!dx && !dy) continue;
         const int ii = i + dx, jj = j + dy;
         if (ii < 0 || ii >= L.nx || jj < 0 || jj >= L.ny) continue;
         const long long u = v + (long long)dy * L.nx + dx;
-        for (int q = 0; q < 4; ++q) Ht += huber_h(tr[q] - L.p_in[q * V + u], L.delta);
+        for (int q = 0; q < 4; ++q) {
+          const float nb = L.p_in[q * V + u];
+          dH += huber_h(tr[q] - nb, L.delta) - huber_h(xi[q] - nb, L.delta);
+        }
       }
-    const float phit = fmaf(0.5f, rs.phi, L.beta * Ht);
-    accept = phit < phi;
+    // Phi(trial) - Phi(current) < -TAU Phi(current)
+    const float phi = fmaf(0.5f, ns.rr, L.beta * Hc);
+    accept = fmaf(L.beta, dH, ds.dphi) < -TAU * phi;
   }
   if (accept) {
     for (int q = 0; q < 4; ++q) L.p_out[q * V + v] = tr[q];
@@ -617,7 +640,7 @@ int kcs_map_lm_fit(const kcs_kinetics_t* k, int nx, int ny, int nz, const float*
   L.lambda = lambda ? lambda : lam_ws;
   L.beta = beta_h;
   L.delta = delta;
-  const size_t smem = sizeof(float) * LM_THREADS * (k->M + 1);
+  const size_t smem = sizeof(float) * LM_THREADS * (k->M + 1) * 2;
   const unsigned blocks = (unsigned)((V + LM_THREADS - 1) / LM_THREADS);
   float* cur = params;
   float* nxt = pong;

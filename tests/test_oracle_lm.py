@@ -73,7 +73,7 @@ def test_objective_never_increases():
     _, _, _, phi_prev = lm.lm_step(x, maps, lam, ts, te, S.FENG, 0.0, 0.01)
     for _ in range(8):
         maps, lam, acc, phi = lm.lm_step(x, maps, lam, ts, te, S.FENG, 0.0, 0.01)
-        assert np.all(phi <= phi_prev + 1e-12)
+        assert np.all(phi <= phi_prev * (1 + 1e-10))   # same point re-evaluated: rounding only
         phi_prev = phi
 
 
