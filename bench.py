@@ -184,15 +184,22 @@ def run_reference(args):
 
 
 # ------------------------------------------------------------------ GPU arm
-def build_problem(K, torch, dev, seed=0):
+def build_problem(K, torch, dev, seed=0, planes=None):
     """Synthetic PR2 study on the device: true maps -> model TACs -> projection
-    -> Poisson counts (80 % trues, 20 % uniform randoms)."""
+    -> Poisson counts (80 % trues, 20 % uniform randoms).  planes < 127 keeps
+    the central planes only (for small profiler captures)."""
+    import dataclasses
     W = S.WORKLOADS["pr2"]
+    if planes and planes != W.nz:
+        W = dataclasses.replace(W, nz=planes, total_prompts=W.total_prompts * planes / W.nz)
     ts, te = W.frames()
     g = K.Geometry(W.nx, W.ny, W.nz, W.vox_mm, W.n_bins, W.n_angles, W.bin_mm, W.n_subsets)
     kin = K.Kinetics(ts, te, S.FENG)
     dt = torch.tensor(te - ts, dtype=torch.float32, device=dev)
-    xi = torch.from_numpy(S.phantom_pr2(W.nx, W.nz, seed=seed)).to(dev)
+    xi_all = S.phantom_pr2(W.nx, S.WORKLOADS["pr2"].nz, seed=seed)
+    z0 = (xi_all.shape[1] - W.nz) // 2
+    xi = torch.from_numpy(np.ascontiguousarray(xi_all[:, z0:z0 + W.nz])).to(dev)
+    del xi_all
     Ft = K.tac_eval(kin, xi)
     ybar = K.forward_project(g, Ft)
     del Ft, xi
@@ -221,7 +228,7 @@ def run_ours(args):
     if world > 1:
         import torch.distributed as dist
         dist.init_process_group("nccl")
-    W, g, kin, dt, kappa, counts, r = build_problem(K, torch, dev, seed=rank)
+    W, g, kin, dt, kappa, counts, r = build_problem(K, torch, dev, seed=rank, planes=args.planes)
     M = W.n_frames
     x = K.init_image(g, dt, kappa, counts, r)
     params = torch.empty((4, W.nz, W.ny, W.nx), device=dev)
@@ -334,7 +341,8 @@ def run_ours(args):
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(total_ms / args.steps, 3),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
         "data": "synthetic",
-        "config": {"workload": WORKLOAD, "voxels": V, "frames": M, "subsets": S_, "lm_steps": N_LM,
+        "config": {"workload": WORKLOAD if W.nz == 127 else f"{WORKLOAD} [{W.nz} central planes]",
+                   "voxels": V, "frames": M, "subsets": S_, "lm_steps": N_LM,
                    "l2": "inputs larger than L2 (image series 1.44 GB, counts 1.06 GB)",
                    "randoms": "uniform per frame"},
         "roofline": roof,
@@ -361,6 +369,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--planes", type=int, default=127,
+                    help="central planes of the workload (127 = full; fewer for profiler captures)")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)
