@@ -174,6 +174,28 @@ int kcs_map_lm_fit(const kcs_kinetics_t* k, int nx, int ny, int nz, const float*
                    float* params, float* lambda, int n_steps, float beta_h, float delta,
                    float* F_out, void* workspace, size_t ws_bytes, void* stream);
 
+/* ------------------------------------------------- MAP-LM without allocation
+ * The paper has no counterpart to this entry point; it exists for callers that
+ * cannot allocate device memory: an application that owns all device memory
+ * through its own pool and forbids raw allocations by plug-ins, or a service
+ * that must not allocate after start-up.  It is kcs_map_lm_fit with the
+ * workspace replaced by a fixed array inside the library (about 5 MB, held on
+ * every GPU that loads the library until the process exits), so it takes no
+ * workspace argument and never allocates.
+ *  - At most KCS_LM_STATIC_MAX_VOXELS voxels (nx*ny*nz); larger problems are
+ *    rejected with KCS_ERR_INVALID_ARG and a message (use kcs_map_lm_fit).
+ *  - The first call on a device looks up the array's device address with that
+ *    device current; make that first call before any stream capture.
+ *  - Every call on a device shares the one array: calls whose work overlaps on
+ *    the GPU (different streams, or host threads without ordering) race and
+ *    corrupt each other; serialise them.  Nothing in the array needs to start at
+ *    zero (each step writes what it later reads).
+ * Arguments as for kcs_map_lm_fit. */
+#define KCS_LM_STATIC_MAX_VOXELS 262144
+int kcs_map_lm_fit_static(const kcs_kinetics_t* k, int nx, int ny, int nz, const float* x,
+                          float* params, float* lambda, int n_steps, float beta_h, float delta,
+                          float* F_out, void* stream);
+
 /* --------------------------------------------------------------- ICM
  * A study binds a geometry, a kinetics table and the caller's device buffers;
  * kcs_icm_iterate runs Sec. II-D's alternation on it, all on one stream:

@@ -65,6 +65,7 @@ SIGNATURES = {
     "kcs_huber_grad": (i32, [i32, i32, i32, vp, f32, vp, vp]),
     "kcs_lm_workspace_size": (sz, [i32, i32, i32]),
     "kcs_map_lm_fit": (i32, [vp, i32, i32, i32, vp, vp, vp, i32, f32, f32, vp, vp, sz, vp]),
+    "kcs_map_lm_fit_static": (i32, [vp, i32, i32, i32, vp, vp, vp, i32, f32, f32, vp, vp]),
     "kcs_study_workspace_size": (sz, [vp, i32]),
     "kcs_create_study": (i32, [pp, C.POINTER(StudyDesc)]),
     "kcs_destroy_study": (i32, [vp]),

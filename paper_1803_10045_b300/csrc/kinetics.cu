@@ -18,6 +18,7 @@
 
 #include <cmath>
 #include <algorithm>
+#include <mutex>
 
 #include "kcs_internal.cuh"
 
@@ -659,3 +660,52 @@ int kcs_map_lm_fit(const kcs_kinetics_t* k, int nx, int ny, int nz, const float*
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------- no-allocation MAP-LM
+// kcs_map_lm_fit_static: the MAP-LM fit with its scratch (ping-pong maps and
+// lambda) in a fixed device array owned by this library, for callers that may
+// not allocate device memory themselves.  The array lives in every GPU that
+// loads the library until the process exits.
+namespace {
+constexpr size_t kStaticLmBytes =
+    ((4 * (size_t)KCS_LM_STATIC_MAX_VOXELS * sizeof(float) + 255) & ~size_t(255)) +
+    (size_t)KCS_LM_STATIC_MAX_VOXELS * sizeof(float);
+static __device__ __align__(256) unsigned char g_lm_scratch[kStaticLmBytes];
+constexpr int kMaxDevices = 64;
+std::mutex g_lm_scratch_mu;
+void* g_lm_scratch_dev[kMaxDevices] = {};   // device address of g_lm_scratch, per device
+}  // namespace
+
+extern "C" int kcs_map_lm_fit_static(const kcs_kinetics_t* k, int nx, int ny, int nz,
+                                     const float* x, float* params, float* lambda, int n_steps,
+                                     float beta_h, float delta, float* F_out, void* stream) {
+  clear_error();
+  KCS_REQUIRE(nx > 0 && ny > 0 && nz > 0, "sizes must be positive");
+  const long long V = (long long)nx * ny * nz;
+  KCS_REQUIRE(V <= KCS_LM_STATIC_MAX_VOXELS,
+              "kcs_map_lm_fit_static handles at most %d voxels (got %lld); use kcs_map_lm_fit "
+              "with a caller workspace", KCS_LM_STATIC_MAX_VOXELS, V);
+  KCS_REQUIRE(kcs_lm_workspace_size(nx, ny, nz) <= kStaticLmBytes, "static scratch too small");
+  int dev = 0;
+  KCS_CUDA(cudaGetDevice(&dev));
+  KCS_REQUIRE(dev >= 0 && dev < kMaxDevices, "device index %d out of range", dev);
+  void* scratch = nullptr;
+  {
+    // First call on this device: look up the array's device address with the
+    // device current (host code cannot use the symbol itself as a pointer).
+    std::lock_guard<std::mutex> lock(g_lm_scratch_mu);
+    if (!g_lm_scratch_dev[dev]) {
+      void* p = nullptr;
+      const cudaError_t e = cudaGetSymbolAddress(&p, g_lm_scratch);
+      if (e != cudaSuccess || !p) {
+        set_error("cudaGetSymbolAddress of the static LM scratch failed: %s",
+                  cudaGetErrorString(e));
+        return KCS_ERR_CUDA;
+      }
+      g_lm_scratch_dev[dev] = p;
+    }
+    scratch = g_lm_scratch_dev[dev];
+  }
+  return kcs_map_lm_fit(k, nx, ny, nz, x, params, lambda, n_steps, beta_h, delta, F_out, scratch,
+                        kStaticLmBytes, stream);
+}
