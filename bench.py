@@ -37,7 +37,15 @@ import kcs_synth as S  # noqa: E402
 METRIC = "ICM iter/s at 344²×127×24 frames"
 WORKLOAD = "PR2: 344x344x127 (2.09 mm), 344 bins x 252 angles, 24 frames, 21 subsets, 10 LM steps/iter"
 N_LM = 10
-BETA_KP, BETA_H, DELTA = 0.1, 0.1, 0.01
+BETA_H, DELTA = 0.1, 0.01
+# The kinetics-derived prior competes with kappa dt sens in the OSL denominator,
+# so its weight scales with the count calibration: beta_kp = 0.1 kappa / kappa_PR1
+# gives PR2 the prior-to-data ratio of config PR1 (beta_kp = 0.1 at kappa ~ 5e-3).
+KAPPA_PR1 = 5.06e-3
+
+
+def beta_kp_for(kappa):
+    return 0.1 * kappa / KAPPA_PR1
 FP32_LANES_PER_SM, N_SM = 128, 148
 # Nominal float32 FLOPs of one MAP-LM voxel-step on this workload: 15 Horner
 # channels x 2 flop x (sum over the 24 intervals of K = 12 + ceil(2.72 a D) at
@@ -145,7 +153,7 @@ def _oracle_sample_inner(reps=1, seed=0):
     og.P(k)                                    # system matrix of the subset (setup)
     for _ in range(reps):
         t0 = time.perf_counter()
-        OO.osl_update(og, x, k, counts_k, 1.0, dt, F=F, beta=BETA_KP)
+        OO.osl_update(og, x, k, counts_k, 1.0, dt, F=F, beta=beta_kp_for(1.0))
         t1 = time.perf_counter()
         OL.lm_step(lm_x, lm_maps, lam, ts, te, S.FENG, BETA_H, DELTA)
         t2 = time.perf_counter()
@@ -234,8 +242,9 @@ def run_ours(args):
     params = torch.empty((4, W.nz, W.ny, W.nx), device=dev)
     params[:] = torch.tensor(S.XI0, device=dev)[:, None, None, None]
     F = torch.zeros_like(x)
+    beta_kp = beta_kp_for(kappa)
     st = K.Study(g, kin, dt, kappa, counts, x, params, F=F, randoms=r, n_lm=N_LM,
-                 beta_kp=BETA_KP, beta_h=BETA_H, delta=DELTA)
+                 beta_kp=beta_kp, beta_h=BETA_H, delta=DELTA)
     for _ in range(args.warmup):
         st.iterate(1)
     torch.cuda.synchronize()
@@ -255,7 +264,7 @@ def run_ours(args):
             rk = rhos[g.n_sub(k)]
             K.osl_ratio(g, k, x, dt, kappa, counts, r, out=rk)
             marks.append(("fwd_ratio", ev()))
-            K.osl_backproject(g, k, x, dt, kappa, rk, F=F, beta=BETA_KP)
+            K.osl_backproject(g, k, x, dt, kappa, rk, F=F, beta=beta_kp)
             marks.append(("bwd_osl", ev()))
         K.map_lm_fit(kin, x, params, N_LM, BETA_H, DELTA, workspace=lm_ws)
         marks.append(("lm_step", ev()))
@@ -344,7 +353,8 @@ def run_ours(args):
         "config": {"workload": WORKLOAD if W.nz == 127 else f"{WORKLOAD} [{W.nz} central planes]",
                    "voxels": V, "frames": M, "subsets": S_, "lm_steps": N_LM,
                    "l2": "inputs larger than L2 (image series 1.44 GB, counts 1.06 GB)",
-                   "randoms": "uniform per frame"},
+                   "randoms": "uniform per frame", "beta_kp": beta_kp, "beta_h": BETA_H,
+                   "delta": DELTA},
         "roofline": roof,
         "kernels": kernels,
         "voxel_lm_fits_per_s": round(V / (N_LM * lm_ms * 1e-3), 1),

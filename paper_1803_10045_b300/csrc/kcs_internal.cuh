@@ -52,10 +52,12 @@ inline cudaStream_t as_stream(void* s) { return reinterpret_cast<cudaStream_t>(s
 // fractional minor index fr = fma(bf, beta, fma(tf, gamma, (n_minor-1)/2)).
 // x-major angles step over columns (minor = rows), the others over rows.
 struct AngleTab {
-  float beta;   // d fr / d bin
-  float gamma;  // d fr / d major step
-  float w;      // step weight h / max(|cos|, |sin|)
-  int xmajor;   // 1: major axis = columns
+  float beta;      // d fr / d bin
+  float gamma;     // d fr / d major step
+  float w;         // step weight h / max(|cos|, |sin|)
+  int xmajor;      // 1: major axis = columns
+  float inv_beta;  // 1 / beta (only to bound candidate bins; exact tests use beta)
+  float pad[3];
 };
 
 }  // namespace kcs
@@ -82,7 +84,16 @@ inline const int* subset_dev(const kcs_geometry* g, int k) {
 inline size_t align256(size_t n) { return (n + 255) & ~size_t(255); }
 
 // ------------------------------------------------------------ kinetics
-constexpr int KMAX = 64;        // series terms per interval (max)
+// Each a-dependent channel is e^{-aD} sum_n a^n c_n with c_n >= 0.  The series
+// is tabulated around NCENT expansion centres a0 = c * DCENT (Taylor shift of the
+// float64 base series, again non-negative coefficients), so a voxel sums at most
+// 13 terms in delta = a - a0 in [0, DCENT) whatever a is.  Table layout
+// [interval][term][part][centre] (part = 4 channels): the lanes of a warp, each
+// on its own centre, read one short contiguous run per load.
+constexpr int NB = 128;         // base terms tabulated in float64
+constexpr int KC = 16;          // terms per centre
+constexpr int NCENT = 15;       // centres 0, 0.25, ..., 3.5 (valid for 0 <= a < 3.75)
+constexpr float DCENT = 0.25f;
 constexpr int NCH = 12;         // channels per term, padded to 3 float4
 constexpr double DT_MAX = 5.0;  // longest propagation interval (min)
 
@@ -90,7 +101,7 @@ constexpr double DT_MAX = 5.0;  // longest propagation interval (min)
 enum { CH_M1 = 0, CH_G, CH_M2, CH_H, CH_M3, CH_D1, CH_GP, CH_D2, CH_HP, CH_D3 };
 
 struct KinDev {
-  const float4* coef;   // [n_iv][KMAX][3] float4 (12 channels)
+  const float4* coef;   // [n_iv][KC][3][NCENT] float4 (12 channels = 3 parts)
   const float* iv_dt;   // [n_iv] interval length (min)
   const int* iv_code;   // [n_iv]: -1 gap, else 2*frame + (last piece of the frame)
   const float* fr_cp;   // [M] frame average of Cp
@@ -110,7 +121,8 @@ struct kcs_kinetics {
   int* d_iv_code;
   float* d_fr_cp;
   float* d_fr_inv;
-  double* d_tmp;  // per-interval doubles used while tabulating
+  double* d_tmp;   // per-interval doubles used while tabulating
+  double* d_base;  // [n_iv][NB][10] float64 base series
   kcs::KinDev dev() const {
     return kcs::KinDev{d_coef, d_iv_dt, d_iv_code, d_fr_cp, d_fr_inv, n_iv, M};
   }

@@ -13,8 +13,9 @@
 // (10 channels).  A series of positive terms has no cancellation, is smooth
 // through a -> 0 and a -> any input exponent, and gives d/da in closed form.
 // The coefficients (input moments) are tabulated once per frame schedule in
-// float64 by Gauss-Legendre quadrature; each voxel then evaluates, per
-// interval, one exp and Horner recurrences of K(aD) terms in float32.
+// float64 by Gauss-Legendre quadrature and re-expanded around 15 centres a0;
+// each voxel then evaluates, per interval, one exp and Horner recurrences of at
+// most 16 terms in delta = a - a0 >= 0 in float32.
 
 #include <cmath>
 #include <algorithm>
@@ -32,7 +33,7 @@ struct TabArgs {
   const double* gl_w;    // [NGL] weights
   int n_gl, n_panel;
   double A1, A2, A3, l1, l2, l3;
-  float* coef;           // [n_iv][KMAX][NCH]
+  double* base;          // [n_iv][NB][10]
   double* m0;            // [n_iv] int_0^D c(u) du
 };
 
@@ -49,10 +50,10 @@ __device__ double feng_cp(double t, const TabArgs& a) {
 __global__ void k_tabulate(TabArgs a) {
   const int iv = blockIdx.x;
   const int n = threadIdx.x;
-  if (n >= KMAX) return;
+  if (n >= NB) return;
   const double D = a.iv_dt[iv];
   const double t0 = a.iv_t0[iv];
-  double P[KMAX + 4], Q[KMAX + 4];   // u^j/j!, v^k/k!
+  double P[NB + 4], Q[NB + 4];   // u^j/j!, v^k/k!
   double m1 = 0, d1 = 0, m2 = 0, d2 = 0, m3 = 0, d3 = 0, s0 = 0;
   const double hp = D / a.n_panel;
   for (int pnl = 0; pnl < a.n_panel; ++pnl) {
@@ -90,20 +91,43 @@ __global__ void k_tabulate(TabArgs a) {
   for (int j = 1; j <= n + 1; ++j) f1 *= D / j;
   const double f2 = f1 * D / (n + 2);
   const double f3 = f2 * D / (n + 3);
-  float* o = a.coef + ((size_t)iv * KMAX + n) * NCH;
-  o[CH_M1] = (float)m1;
-  o[CH_G] = (float)f1;
-  o[CH_M2] = (float)m2;
-  o[CH_H] = (float)(f2 * (n + 1));
-  o[CH_M3] = (float)m3;
-  o[CH_D1] = (float)d1;
-  o[CH_GP] = (float)f2;
-  o[CH_D2] = (float)d2;
-  o[CH_HP] = (float)(f3 * (n + 1));
-  o[CH_D3] = (float)d3;
-  o[10] = 0.f;
-  o[11] = 0.f;
+  double* o = a.base + ((size_t)iv * NB + n) * 10;
+  o[CH_M1] = m1;
+  o[CH_G] = f1;
+  o[CH_M2] = m2;
+  o[CH_H] = f2 * (n + 1);
+  o[CH_M3] = m3;
+  o[CH_D1] = d1;
+  o[CH_GP] = f2;
+  o[CH_D2] = d2;
+  o[CH_HP] = f3 * (n + 1);
+  o[CH_D3] = d3;
   if (n == 0) a.m0[iv] = s0;
+}
+
+// Taylor shift of every channel to the centres a0 = c DCENT: with
+// sum_n a^n b_n = sum_j (a - a0)^j s_j,  s_j = sum_{n >= j} C(n, j) a0^{n-j} b_n,
+// a sum of non-negative terms.  One block per (interval, centre), one thread per
+// (term j, channel).
+__global__ void k_shift(const double* base, float* coef) {
+  const int iv = blockIdx.x / NCENT;
+  const int c = blockIdx.x % NCENT;
+  const int j = threadIdx.x / 10;
+  const int ch = threadIdx.x % 10;
+  if (j >= KC) return;
+  const double a0 = c * (double)DCENT;
+  const double* b = base + (size_t)iv * NB * 10;
+  double r = 1.0, sum = 0.0;   // r = C(j+m, j) a0^m
+  for (int m = 0; j + m < NB; ++m) {
+    sum += r * b[(size_t)(j + m) * 10 + ch];
+    r *= a0 * (double)(j + m + 1) / (double)(m + 1);
+  }
+  float* o = coef + (((size_t)iv * KC + j) * 3 * NCENT) * 4;   // [iv][j][part][centre][4]
+  o[((ch / 4) * NCENT + c) * 4 + ch % 4] = (float)sum;
+  if (ch == 0) {
+    o[(2 * NCENT + c) * 4 + 2] = 0.f;
+    o[(2 * NCENT + c) * 4 + 3] = 0.f;
+  }
 }
 
 __global__ void k_frame_tables(const double* m0, const int* code, int n_iv, const double* fdt,
@@ -118,80 +142,119 @@ __global__ void k_frame_tables(const double* m0, const int* code, int n_iv, cons
 }
 
 // ---------------------------------------------------------------- model
-// Evaluates F_m (and dF_m/d(K1,k2,k3,Vb) when JAC) frame by frame and hands
-// each finished frame to sink(m, F, J0, J1, J2, J3).
-template <bool JAC, class Sink>
-__device__ __forceinline__ void eval_model(const KinDev& kd, float K1, float k2, float k3, float Vb,
-                                           Sink& sink) {
-  const float a = k2 + k3;
-  float I = 0.f, Ip = 0.f, Jr = 0.f, Jp = 0.f;
-  float SA = 0.f, SB = 0.f, SAp = 0.f, SBp = 0.f;
+// Number of series terms for y = delta D: the smallest K with y^K / K! <= 1e-8
+// is bounded above by ceil(2 y + 5.75 sqrt(y) + 3.75) for 0 <= y <= 17.5
+// (checked on a fine grid of y); every channel's coefficients satisfy
+// c_n <= c_0 D^n / n!, so the truncated tail is below 1e-8 of the sum.
+__device__ __forceinline__ int series_terms(float y) {
+  return (int)ceilf(fmaf(2.0f, y, fmaf(5.75f, sqrtf(y), 3.75f)));
+}
+
+// Horner evaluation of the 5 value channels (and the 5 derivative channels when
+// JAC) of one voxel from a table row set tab (KC terms x 3 float4) at delta.
+struct Series {
+  float m1, g, m2, h, m3, d1, gp, d2, hp, d3;
+};
+
+// Evaluates F_m (and dF_m/d(K1,k2,k3,Vb) when JAC) of VPT voxels frame by frame
+// and hands each finished frame to sink(v, m, F, J0, J1, J2, J3).  Each voxel
+// sums its series around its own centre (delta < DCENT, at most 13 terms).
+template <int VPT, bool JAC, class Sink>
+__device__ __forceinline__ void eval_model(const KinDev& kd, const float (&K1)[VPT],
+                                           const float (&k2)[VPT], const float (&k3)[VPT],
+                                           const float (&Vb)[VPT], Sink& sink) {
+  const unsigned mask = __activemask();
+  float a[VPT], dl[VPT], I[VPT], Ip[VPT], Jr[VPT], Jp[VPT], SA[VPT], SB[VPT], SAp[VPT], SBp[VPT];
+  int cen[VPT];
+#pragma unroll
+  for (int v = 0; v < VPT; ++v) {
+    a[v] = fmaxf(k2[v] + k3[v], 0.f);
+    I[v] = Ip[v] = Jr[v] = Jp[v] = SA[v] = SB[v] = SAp[v] = SBp[v] = 0.f;
+    cen[v] = min(NCENT - 1, (int)(a[v] * (1.0f / DCENT)));
+    dl[v] = a[v] - (float)cen[v] * DCENT;
+  }
   for (int iv = 0; iv < kd.n_iv; ++iv) {
     const float D = __ldg(kd.iv_dt + iv);
-    const float y = a * D;
-    const int K = min(KMAX, (int)ceilf(2.72f * y) + 12);
-    const float4* c = kd.coef + (size_t)iv * KMAX * 3;
-    // Horner from the highest term down.
-    float p_m1 = 0.f, p_g = 0.f, p_m2 = 0.f, p_h = 0.f, p_m3 = 0.f;
-    float p_d1 = 0.f, p_gp = 0.f, p_d2 = 0.f, p_hp = 0.f, p_d3 = 0.f;
+    int K = 0;
+#pragma unroll
+    for (int v = 0; v < VPT; ++v) K = max(K, series_terms(dl[v] * D));
+    K = min(KC, __reduce_max_sync(mask, K));   // one trip count per warp
+    const float4* tab = kd.coef + (size_t)iv * KC * 3 * NCENT;
+    Series p[VPT];
+#pragma unroll
+    for (int v = 0; v < VPT; ++v) p[v] = Series{0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+#pragma unroll 2
     for (int n = K - 1; n >= 0; --n) {
-      const float4 c0 = __ldg(c + 3 * n);
-      const float4 c1 = __ldg(c + 3 * n + 1);
-      p_m1 = fmaf(p_m1, a, c0.x);
-      p_g = fmaf(p_g, a, c0.y);
-      p_m2 = fmaf(p_m2, a, c0.z);
-      p_h = fmaf(p_h, a, c0.w);
-      p_m3 = fmaf(p_m3, a, c1.x);
-      if (JAC) {
-        const float4 c2 = __ldg(c + 3 * n + 2);
-        p_d1 = fmaf(p_d1, a, c1.y);
-        p_gp = fmaf(p_gp, a, c1.z);
-        p_d2 = fmaf(p_d2, a, c1.w);
-        p_hp = fmaf(p_hp, a, c2.x);
-        p_d3 = fmaf(p_d3, a, c2.y);
+      const float4* row = tab + (size_t)n * 3 * NCENT;
+      float4 c0, c1, c2;
+#pragma unroll
+      for (int v = 0; v < VPT; ++v) {
+        if (v == 0 || cen[v] != cen[v - 1]) {   // the voxels of a thread often share a centre
+          c0 = __ldg(row + cen[v]);
+          c1 = __ldg(row + NCENT + cen[v]);
+          c2 = JAC ? __ldg(row + 2 * NCENT + cen[v]) : make_float4(0.f, 0.f, 0.f, 0.f);
+        }
+        const float d = dl[v];
+        p[v].m1 = fmaf(p[v].m1, d, c0.x);
+        p[v].g = fmaf(p[v].g, d, c0.y);
+        p[v].m2 = fmaf(p[v].m2, d, c0.z);
+        p[v].h = fmaf(p[v].h, d, c0.w);
+        p[v].m3 = fmaf(p[v].m3, d, c1.x);
+        if (JAC) {
+          p[v].d1 = fmaf(p[v].d1, d, c1.y);
+          p[v].gp = fmaf(p[v].gp, d, c1.z);
+          p[v].d2 = fmaf(p[v].d2, d, c1.w);
+          p[v].hp = fmaf(p[v].hp, d, c2.x);
+          p[v].d3 = fmaf(p[v].d3, d, c2.y);
+        }
       }
     }
-    const float E = expf(-y);
-    const float G = E * p_g, H = E * p_h;
-    const float A = fmaf(I, G, E * p_m2);
-    const float B = fmaf(Jr, D, fmaf(I, H, E * p_m3));
     const int code = __ldg(kd.iv_code + iv);
-    if (JAC) {
-      const float Gp = -E * p_gp, Hp = -E * p_hp;
-      const float Ap = fmaf(Ip, G, fmaf(I, Gp, -E * p_d2));
-      const float Bp = fmaf(Jp, D, fmaf(Ip, H, fmaf(I, Hp, -E * p_d3)));
-      Ip = fmaf(E, fmaf(-D, I, Ip), -E * p_d1);
-      Jp += Ap;
-      if (code >= 0) {   // gaps between frames propagate the state only
-        SAp += Ap;
-        SBp += Bp;
-      }
-    }
-    I = fmaf(E, I, E * p_m1);
-    Jr += A;
-    if (code >= 0) {
-      SA += A;
-      SB += B;
-    }
-    if (code >= 0 && (code & 1)) {
-      const int m = code >> 1;
-      const float inv = __ldg(kd.fr_inv + m);
-      const float cp = __ldg(kd.fr_cp + m);
-      const float S = fmaf(k3, SB, SA) * inv;   // frame average of C_T / K1
-      const float T = K1 * S;
-      const float F = fmaf(Vb, cp - T, T);      // (1 - Vb) T + Vb cp
+    const bool in_frame = code >= 0;             // gaps propagate the state only
+    const bool frame_end = in_frame && (code & 1);
+    const int m = code >> 1;
+    const float inv = frame_end ? __ldg(kd.fr_inv + m) : 0.f;
+    const float cpf = frame_end ? __ldg(kd.fr_cp + m) : 0.f;
+#pragma unroll
+    for (int v = 0; v < VPT; ++v) {
+      const float E = expf(-a[v] * D);
+      const float G = E * p[v].g, H = E * p[v].h;
+      const float A = fmaf(I[v], G, E * p[v].m2);
+      const float B = fmaf(Jr[v], D, fmaf(I[v], H, E * p[v].m3));
       if (JAC) {
-        // dC_T/dk2 = K1 (dI/da + k3 dJ/da); dC_T/dk3 = K1 (dI/da + J + k3 dJ/da),
-        // and dI/da + J = -a dJ/da (from I' = Cp - a I), so dC_T/dk3 = -K1 k2 dJ/da:
-        // a single non-negative term, exactly 0 at k2 = 0 instead of a cancelling
-        // difference.
-        const float w = 1.f - Vb;
-        const float Sp = fmaf(k3, SBp, SAp) * inv;
-        sink(m, F, w * S, w * K1 * Sp, -w * K1 * k2 * SBp * inv, cp - T);
-      } else {
-        sink(m, F, 0.f, 0.f, 0.f, 0.f);
+        const float Gp = -E * p[v].gp, Hp = -E * p[v].hp;
+        const float Ap = fmaf(Ip[v], G, fmaf(I[v], Gp, -E * p[v].d2));
+        const float Bp = fmaf(Jp[v], D, fmaf(Ip[v], H, fmaf(I[v], Hp, -E * p[v].d3)));
+        Ip[v] = fmaf(E, fmaf(-D, I[v], Ip[v]), -E * p[v].d1);
+        Jp[v] += Ap;
+        if (in_frame) {
+          SAp[v] += Ap;
+          SBp[v] += Bp;
+        }
       }
-      SA = SB = SAp = SBp = 0.f;
+      I[v] = fmaf(E, I[v], E * p[v].m1);
+      Jr[v] += A;
+      if (in_frame) {
+        SA[v] += A;
+        SB[v] += B;
+      }
+      if (frame_end) {
+        const float S = fmaf(k3[v], SB[v], SA[v]) * inv;   // frame average of C_T / K1
+        const float T = K1[v] * S;
+        const float F = fmaf(Vb[v], cpf - T, T);           // (1 - Vb) T + Vb cp
+        if (JAC) {
+          // dC_T/dk2 = K1 (dI/da + k3 dJ/da); dC_T/dk3 = K1 (dI/da + J + k3 dJ/da),
+          // and dI/da + J = -a dJ/da (from I' = Cp - a I), so dC_T/dk3 = -K1 k2 dJ/da:
+          // a single non-negative term, exactly 0 at k2 = 0 instead of a cancelling
+          // difference.
+          const float w = 1.f - Vb[v];
+          const float Sp = fmaf(k3[v], SBp[v], SAp[v]) * inv;
+          sink(v, m, F, w * S, w * K1[v] * Sp, -w * K1[v] * k2[v] * SBp[v] * inv, cpf - T);
+        } else {
+          sink(v, m, F, 0.f, 0.f, 0.f, 0.f);
+        }
+        SA[v] = SB[v] = SAp[v] = SBp[v] = 0.f;
+      }
     }
   }
 }
@@ -202,7 +265,7 @@ constexpr int TAC_THREADS = 128;
 struct TacSink {
   float* sF;   // shared row of this voxel: M floats
   float* sJ;   // shared row: 4M floats, or null
-  __device__ void operator()(int m, float F, float j0, float j1, float j2, float j3) {
+  __device__ void operator()(int, int m, float F, float j0, float j1, float j2, float j3) {
     sF[m] = F;
     if (sJ) {
       sJ[4 * m + 0] = j0;
@@ -227,10 +290,10 @@ __global__ void __launch_bounds__(TAC_THREADS) k_tac_eval(KinDev kd, long long n
   const long long v = v0 + threadIdx.x;
   const long long nv = min((long long)TAC_THREADS, n_vox - v0);
   if (v < n_vox) {
-    const float K1 = params[v], k2 = params[n_vox + v], k3 = params[2 * n_vox + v],
-                Vb = params[3 * n_vox + v];
+    const float K1[1] = {params[v]}, k2[1] = {params[n_vox + v]}, k3[1] = {params[2 * n_vox + v]},
+                Vb[1] = {params[3 * n_vox + v]};
     TacSink sink{sF + threadIdx.x * ldF, JAC ? sJ + threadIdx.x * ldJ : nullptr};
-    eval_model<JAC>(kd, K1, k2, k3, Vb, sink);
+    eval_model<1, JAC>(kd, K1, k2, k3, Vb, sink);
   }
   __syncthreads();
   for (long long e = threadIdx.x; e < nv * M; e += TAC_THREADS) {
@@ -299,6 +362,8 @@ __global__ void k_huber_grad(int nx, int ny, int nz, const float* p, float delta
 
 // ---------------------------------------------------------------- MAP-LM
 constexpr int LM_THREADS = 128;
+constexpr int LM_VPT = 2;                       // voxels per thread
+constexpr int LM_BLOCK_VOX = LM_THREADS * LM_VPT;
 __constant__ float c_lo[4] = {0.f, 0.f, 0.f, 0.f};
 __constant__ float c_hi[4] = {2.f, 2.f, 1.f, 1.f};
 constexpr float LAMBDA0 = 1e-2f, LAMBDA_MIN = 1e-7f, LAMBDA_MAX = 1e7f;
@@ -317,21 +382,28 @@ struct LmArgs {
   float beta, delta;
 };
 
-struct NormalSink {
-  const float* xs;   // this voxel's TAC in shared memory
-  float* fc;         // this voxel's model TAC at the current point (shared memory)
-  float rr;          // sum of squared residuals at the current point
+// Damped normal equations of one voxel, accumulated frame by frame in float32.
+struct Normal {
   float A00, A01, A02, A03, A11, A12, A13, A22, A23, A33;
   float b0, b1, b2, b3;
-  __device__ void operator()(int m, float F, float j0, float j1, float j2, float j3) {
-    const float r = xs[m] - F;
-    fc[m] = F;
-    rr = fmaf(r, r, rr);
-    A00 = fmaf(j0, j0, A00); A01 = fmaf(j0, j1, A01); A02 = fmaf(j0, j2, A02); A03 = fmaf(j0, j3, A03);
-    A11 = fmaf(j1, j1, A11); A12 = fmaf(j1, j2, A12); A13 = fmaf(j1, j3, A13);
-    A22 = fmaf(j2, j2, A22); A23 = fmaf(j2, j3, A23);
-    A33 = fmaf(j3, j3, A33);
-    b0 = fmaf(j0, r, b0); b1 = fmaf(j1, r, b1); b2 = fmaf(j2, r, b2); b3 = fmaf(j3, r, b3);
+  float rr;   // sum of squared residuals at the current point
+};
+
+struct NormalSink {
+  const float* xs[LM_VPT];   // the voxels' TACs in shared memory
+  float* fc[LM_VPT];         // their model TACs at the current point (shared memory)
+  Normal n[LM_VPT];
+  __device__ void operator()(int v, int m, float F, float j0, float j1, float j2, float j3) {
+    const float r = xs[v][m] - F;
+    fc[v][m] = F;
+    Normal& s = n[v];
+    s.rr = fmaf(r, r, s.rr);
+    s.A00 = fmaf(j0, j0, s.A00); s.A01 = fmaf(j0, j1, s.A01); s.A02 = fmaf(j0, j2, s.A02);
+    s.A03 = fmaf(j0, j3, s.A03); s.A11 = fmaf(j1, j1, s.A11); s.A12 = fmaf(j1, j2, s.A12);
+    s.A13 = fmaf(j1, j3, s.A13); s.A22 = fmaf(j2, j2, s.A22); s.A23 = fmaf(j2, j3, s.A23);
+    s.A33 = fmaf(j3, j3, s.A33);
+    s.b0 = fmaf(j0, r, s.b0); s.b1 = fmaf(j1, r, s.b1); s.b2 = fmaf(j2, r, s.b2);
+    s.b3 = fmaf(j3, r, s.b3);
   }
 };
 
@@ -340,18 +412,18 @@ struct NormalSink {
 // accumulated directly so that small decreases are not lost in the rounding of
 // two large sums.
 struct DeltaSink {
-  const float* xs;
-  const float* fc;
-  float dphi;
-  __device__ void operator()(int m, float F, float, float, float, float) {
-    const float Fc = fc[m];
-    dphi = fmaf(Fc - F, xs[m] - 0.5f * (Fc + F), dphi);
+  const float* xs[LM_VPT];
+  const float* fc[LM_VPT];
+  float dphi[LM_VPT];
+  __device__ void operator()(int v, int m, float F, float, float, float, float) {
+    const float Fc = fc[v][m];
+    dphi[v] = fmaf(Fc - F, xs[v][m] - 0.5f * (Fc + F), dphi[v]);
   }
 };
 
 // Cholesky solve of the damped 4x4 normal equations in float64.  Returns
 // false (no step) if a pivot is not positive.
-__device__ bool solve4(const NormalSink& s, double lam, const double rhs[4], double out[4]) {
+__device__ bool solve4(const Normal& s, double lam, const double rhs[4], double out[4]) {
   const double A00 = (double)s.A00 + lam, A11 = (double)s.A11 + lam, A22 = (double)s.A22 + lam,
                A33 = (double)s.A33 + lam;
   const double A10 = s.A01, A20 = s.A02, A30 = s.A03, A21 = s.A12, A31 = s.A13, A32 = s.A23;
@@ -380,78 +452,106 @@ __device__ bool solve4(const NormalSink& s, double lam, const double rhs[4], dou
   return true;
 }
 
-__global__ void __launch_bounds__(LM_THREADS) k_lm_step(LmArgs L) {
-  extern __shared__ float xs_all[];
-  const int M = L.kd.M;
-  const int ld = M + 1;
-  float* fc_all = xs_all + LM_THREADS * ld;
-  const long long V = (long long)L.nx * L.ny * L.nz;
-  const long long v0 = (long long)blockIdx.x * LM_THREADS;
-  const long long v = v0 + threadIdx.x;
-  const long long nv = min((long long)LM_THREADS, V - v0);
-  for (long long e = threadIdx.x; e < nv * M; e += LM_THREADS) {
-    const long long r = e / M, m = e - r * M;
-    xs_all[r * ld + m] = L.x[v0 * M + e];
-  }
-  __syncthreads();
-  if (v >= V) return;
-  const float* xs = xs_all + threadIdx.x * ld;
-  const int i = (int)(v % L.nx);
-  const int j = (int)((v / L.nx) % L.ny);
-  float xi[4];
-  for (int q = 0; q < 4; ++q) xi[q] = L.p_in[q * V + v];
-  // Huber gradient and potential at the current point (neighbours frozen).
-  float g[4] = {0.f, 0.f, 0.f, 0.f};
-  float Hc = 0.f;
+// Huber gradient of a voxel and the potential of a given point against the
+// frozen neighbours.
+__device__ __forceinline__ void huber_terms(const LmArgs& L, long long V, long long v, int i, int j,
+                                            const float (&pt)[4], float (&g)[4], float& H) {
+  g[0] = g[1] = g[2] = g[3] = 0.f;
+  H = 0.f;
   for (int dy = -1; dy <= 1; ++dy)
     for (int dx = -1; dx <= 1; ++dx) {
       if (!dx && !dy) continue;
       const int ii = i + dx, jj = j + dy;
       if (ii < 0 || ii >= L.nx || jj < 0 || jj >= L.ny) continue;
       const long long u = v + (long long)dy * L.nx + dx;
+#pragma unroll
       for (int q = 0; q < 4; ++q) {
-        const float t = xi[q] - L.p_in[q * V + u];
+        const float t = pt[q] - __ldg(L.p_in + q * V + u);
         g[q] += huber_psi(t, L.delta);
-        Hc += huber_h(t, L.delta);
+        H += huber_h(t, L.delta);
       }
     }
-  float* fc = fc_all + threadIdx.x * ld;
-  NormalSink ns{xs, fc, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-  eval_model<true>(L.kd, xi[0], xi[1], xi[2], xi[3], ns);
-  float lam = L.reset_lambda ? LAMBDA0 : L.lambda[v];
-  const double rhs[4] = {(double)ns.b0 - (double)L.beta * g[0], (double)ns.b1 - (double)L.beta * g[1],
-                         (double)ns.b2 - (double)L.beta * g[2], (double)ns.b3 - (double)L.beta * g[3]};
-  double step[4];
-  bool accept = false;
-  float tr[4];
-  if (solve4(ns, (double)lam, rhs, step)) {
-    for (int q = 0; q < 4; ++q) tr[q] = fminf(fmaxf(xi[q] + (float)step[q], c_lo[q]), c_hi[q]);
-    DeltaSink ds{xs, fc, 0.f};
-    eval_model<false>(L.kd, tr[0], tr[1], tr[2], tr[3], ds);
-    float dH = 0.f;   // H(trial) - H(current), neighbours frozen
-    for (int dy = -1; dy <= 1; ++dy)
-      for (int dx = -1; dx <= 1; ++dx) {
-        if (!dx && !dy) continue;
-        const int ii = i + dx, jj = j + dy;
-        if (ii < 0 || ii >= L.nx || jj < 0 || jj >= L.ny) continue;
-        const long long u = v + (long long)dy * L.nx + dx;
-        for (int q = 0; q < 4; ++q) {
-          const float nb = L.p_in[q * V + u];
-          dH += huber_h(tr[q] - nb, L.delta) - huber_h(xi[q] - nb, L.delta);
-        }
-      }
+}
+
+__global__ void __launch_bounds__(LM_THREADS, 4) k_lm_step(LmArgs L) {
+  extern __shared__ float xs_all[];
+  const int M = L.kd.M;
+  const int ld = M + 1;
+  float* fc_all = xs_all + LM_BLOCK_VOX * ld;
+  const long long V = (long long)L.nx * L.ny * L.nz;
+  const long long v0 = (long long)blockIdx.x * LM_BLOCK_VOX;
+  const long long nv = min((long long)LM_BLOCK_VOX, V - v0);
+  for (long long e = threadIdx.x; e < nv * M; e += LM_THREADS) {
+    const long long r = e / M, m = e - r * M;
+    xs_all[r * ld + m] = L.x[v0 * M + e];
+  }
+  __syncthreads();
+  long long vv[LM_VPT];
+  bool act[LM_VPT];
+  float K1[LM_VPT], k2[LM_VPT], k3[LM_VPT], Vb[LM_VPT];
+  NormalSink ns;
+  DeltaSink ds;
+#pragma unroll
+  for (int k = 0; k < LM_VPT; ++k) {
+    const int lv = threadIdx.x + k * LM_THREADS;
+    act[k] = lv < nv;
+    vv[k] = act[k] ? v0 + lv : v0;      // inactive slots shadow a valid voxel, write nothing
+    K1[k] = L.p_in[vv[k]];
+    k2[k] = L.p_in[V + vv[k]];
+    k3[k] = L.p_in[2 * V + vv[k]];
+    Vb[k] = L.p_in[3 * V + vv[k]];
+    ns.xs[k] = xs_all + (act[k] ? lv : 0) * ld;
+    ds.xs[k] = ns.xs[k];
+    ns.fc[k] = fc_all + lv * ld;
+    ds.fc[k] = ns.fc[k];
+    ns.n[k] = Normal{0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+    ds.dphi[k] = 0.f;
+  }
+  eval_model<LM_VPT, true>(L.kd, K1, k2, k3, Vb, ns);
+  float tr[LM_VPT][4], phi[LM_VPT], Hc[LM_VPT], lam[LM_VPT];
+  bool solved[LM_VPT];
+#pragma unroll
+  for (int k = 0; k < LM_VPT; ++k) {
+    const long long v = vv[k];
+    const int i = (int)(v % L.nx);
+    const int j = (int)((v / L.nx) % L.ny);
+    const float xi[4] = {K1[k], k2[k], k3[k], Vb[k]};
+    float g[4];
+    huber_terms(L, V, v, i, j, xi, g, Hc[k]);
+    phi[k] = fmaf(0.5f, ns.n[k].rr, L.beta * Hc[k]);
+    lam[k] = L.reset_lambda ? LAMBDA0 : L.lambda[v];
+    const Normal& n = ns.n[k];
+    const double rhs[4] = {(double)n.b0 - (double)L.beta * g[0], (double)n.b1 - (double)L.beta * g[1],
+                           (double)n.b2 - (double)L.beta * g[2], (double)n.b3 - (double)L.beta * g[3]};
+    double step[4];
+    solved[k] = solve4(n, (double)lam[k], rhs, step);
+#pragma unroll
+    for (int q = 0; q < 4; ++q)
+      tr[k][q] = solved[k] ? fminf(fmaxf(xi[q] + (float)step[q], c_lo[q]), c_hi[q]) : xi[q];
+  }
+  {
+    float t1[LM_VPT], t2[LM_VPT], t3[LM_VPT], t4[LM_VPT];
+#pragma unroll
+    for (int k = 0; k < LM_VPT; ++k) {
+      t1[k] = tr[k][0]; t2[k] = tr[k][1]; t3[k] = tr[k][2]; t4[k] = tr[k][3];
+    }
+    eval_model<LM_VPT, false>(L.kd, t1, t2, t3, t4, ds);
+  }
+#pragma unroll
+  for (int k = 0; k < LM_VPT; ++k) {
+    if (!act[k]) continue;
+    const long long v = vv[k];
+    const int i = (int)(v % L.nx);
+    const int j = (int)((v / L.nx) % L.ny);
+    float gt[4], Ht;
+    huber_terms(L, V, v, i, j, tr[k], gt, Ht);
     // Phi(trial) - Phi(current) < -TAU Phi(current)
-    const float phi = fmaf(0.5f, ns.rr, L.beta * Hc);
-    accept = fmaf(L.beta, dH, ds.dphi) < -TAU * phi;
+    const bool accept = solved[k] && fmaf(L.beta, Ht - Hc[k], ds.dphi[k]) < -TAU * phi[k];
+    const float xi[4] = {K1[k], k2[k], k3[k], Vb[k]};
+#pragma unroll
+    for (int q = 0; q < 4; ++q) L.p_out[q * V + v] = accept ? tr[k][q] : xi[q];
+    L.lambda[v] = accept ? fmaxf(lam[k] * 0.1f, LAMBDA_MIN) : fminf(lam[k] * 10.f, LAMBDA_MAX);
   }
-  if (accept) {
-    for (int q = 0; q < 4; ++q) L.p_out[q * V + v] = tr[q];
-    lam = fmaxf(lam * 0.1f, LAMBDA_MIN);
-  } else {
-    for (int q = 0; q < 4; ++q) L.p_out[q * V + v] = xi[q];
-    lam = fminf(lam * 10.f, LAMBDA_MAX);
-  }
-  L.lambda[v] = lam;
 }
 
 }  // namespace kcs
@@ -526,7 +626,8 @@ int kcs_create_kinetics(kcs_kinetics_t** out, int n_frames, const double* t_star
   gauss_legendre(NGL, gx, gw);
   cudaStream_t s = as_stream(stream);
   const size_t nd = 2 * (size_t)n_iv + 2 * NGL + n_frames + n_iv;
-  bool ok = cudaMalloc(&k->d_coef, sizeof(float) * (size_t)n_iv * KMAX * NCH) == cudaSuccess;
+  bool ok = cudaMalloc(&k->d_coef, sizeof(float) * (size_t)n_iv * NCENT * KC * NCH) == cudaSuccess;
+  ok = ok && cudaMalloc(&k->d_base, sizeof(double) * (size_t)n_iv * NB * 10) == cudaSuccess;
   ok = ok && cudaMalloc(&k->d_iv_dt, sizeof(float) * n_iv) == cudaSuccess;
   ok = ok && cudaMalloc(&k->d_iv_code, sizeof(int) * n_iv) == cudaSuccess;
   ok = ok && cudaMalloc(&k->d_fr_cp, sizeof(float) * n_frames) == cudaSuccess;
@@ -556,9 +657,11 @@ int kcs_create_kinetics(kcs_kinetics_t** out, int n_frames, const double* t_star
   ta.n_panel = NPANEL;
   ta.A1 = feng[0]; ta.A2 = feng[1]; ta.A3 = feng[2];
   ta.l1 = feng[3]; ta.l2 = feng[4]; ta.l3 = feng[5];
-  ta.coef = reinterpret_cast<float*>(k->d_coef);
+  ta.base = k->d_base;
   ta.m0 = k->d_tmp + 2 * n_iv + 2 * NGL + n_frames;
-  k_tabulate<<<n_iv, KMAX, 0, s>>>(ta);
+  k_tabulate<<<n_iv, NB, 0, s>>>(ta);
+  KCS_LAUNCHED();
+  k_shift<<<n_iv * NCENT, KC * 10, 0, s>>>(k->d_base, reinterpret_cast<float*>(k->d_coef));
   KCS_LAUNCHED();
   k_frame_tables<<<1, 32, 0, s>>>(ta.m0, k->d_iv_code, n_iv, k->d_tmp + 2 * n_iv + 2 * NGL,
                                   n_frames, k->d_fr_cp, k->d_fr_inv);
@@ -573,6 +676,7 @@ int kcs_destroy_kinetics(kcs_kinetics_t* k) {
   clear_error();
   if (!k) return KCS_OK;
   cudaFree(k->d_coef);
+  cudaFree(k->d_base);
   cudaFree(k->d_iv_dt);
   cudaFree(k->d_iv_code);
   cudaFree(k->d_fr_cp);
@@ -641,8 +745,9 @@ int kcs_map_lm_fit(const kcs_kinetics_t* k, int nx, int ny, int nz, const float*
   L.lambda = lambda ? lambda : lam_ws;
   L.beta = beta_h;
   L.delta = delta;
-  const size_t smem = sizeof(float) * LM_THREADS * (k->M + 1) * 2;
-  const unsigned blocks = (unsigned)((V + LM_THREADS - 1) / LM_THREADS);
+  const size_t smem = sizeof(float) * LM_BLOCK_VOX * (k->M + 1) * 2;
+  KCS_CUDA(cudaFuncSetAttribute(k_lm_step, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  const unsigned blocks = (unsigned)((V + LM_BLOCK_VOX - 1) / LM_BLOCK_VOX);
   float* cur = params;
   float* nxt = pong;
   for (int it = 0; it < n_steps; ++it) {

@@ -3,11 +3,12 @@
 //
 // Data layout: images [Z][ny][nx][M] and sinograms [Z][A][B][M] keep the M
 // frames of one voxel / bin contiguous, so every sample of a ray moves whole
-// float4 frame quads.  A warp holds 32/MQ rays (forward) or voxels (back), MQ =
-// M/4 lanes each, so one load instruction fetches the contiguous frame vectors
-// of several rays.  The back-projection is a gather: each voxel recomputes the
-// forward's sample positions with the same fused multiply-adds, so the set of
-// (voxel, bin, weight) triples is exactly the forward's, with no atomics.
+// float4 frame quads.  In the forward a warp holds 32/MQ rays, MQ = M/4 lanes
+// each, so one load instruction fetches the contiguous frame vectors of several
+// rays.  The back-projection is a gather: each voxel (one thread, all frames)
+// recomputes the forward's sample positions with the same fused multiply-adds,
+// so the set of (voxel, bin, weight) triples is exactly the forward's, with no
+// atomics; the ratio rows of a voxel tile are staged in shared memory.
 
 #include <cstdarg>
 #include <cmath>
@@ -142,87 +143,165 @@ __global__ void __launch_bounds__(256) k_forward(ProjArgs p) {
   p.yout[oi] = rho;
 }
 
+// Bins whose sample at this major step can land in [m-1, m+1): the real-valued
+// position b*beta + inner differs from the kernels' single fused multiply-add by
+// half an ulp (< 1e-4 of a step at these sizes), so a 1e-3 margin on the
+// real-valued bin interval is conservative; the exact test is made per
+// candidate by the caller.
+__device__ __forceinline__ void bin_range_tight(const AngleTab& T, int m, float inner, float bc,
+                                                int B, int& b_lo, int& b_hi) {
+  float lo = ((float)(m - 1) - inner) * T.inv_beta;
+  float hi = ((float)(m + 1) - inner) * T.inv_beta;
+  if (lo > hi) { const float tmp = lo; lo = hi; hi = tmp; }
+  b_lo = max(0, (int)ceilf(fmaxf(lo + bc - 1e-3f, -2.0f)));
+  b_hi = min(B - 1, (int)floorf(fminf(hi + bc + 1e-3f, (float)B + 2.0f)));
+}
+
 // Bins of angle T whose sample at major step t lands within one minor step of
-// m: the exact test is made per candidate by the caller.
+// m, with one extra bin of margin on each side (used to bound staged tiles):
+// the exact test is made per candidate by the caller.
 __device__ __forceinline__ void bin_range(const AngleTab& T, int m, float inner, float bc, int B,
                                           int& b_lo, int& b_hi) {
-  float lo = ((float)(m - 1) - inner) / T.beta;
-  float hi = ((float)(m + 1) - inner) / T.beta;
+  float lo = ((float)(m - 1) - inner) * T.inv_beta;
+  float hi = ((float)(m + 1) - inner) * T.inv_beta;
   if (lo > hi) { const float tmp = lo; lo = hi; hi = tmp; }
   b_lo = max(0, (int)floorf(fmaxf(lo + bc, -2.0f)) - 1);
   b_hi = min(B - 1, (int)ceilf(fminf(hi + bc, (float)B + 2.0f)) + 1);
 }
 
-// Gather back-projection.  MODE 0: x = P_k^T y.  MODE 1: OSL update of x in
-// place with y = rho (Eq. 2 with the prior of Eq. 3).
+// Tiled gather back-projection: one thread per voxel of a 16 x 16 in-plane
+// tile, all frames per thread (the candidate-bin geometry is computed once per
+// voxel and angle).  The ratio rows the tile can touch are staged in shared
+// memory, up to BK_ACHUNK angles at a time, with an odd 16-byte row pitch so
+// that the per-thread 128-bit reads of different rows fall in different banks.
+// MODE 0: x = P_k^T y.  MODE 1: OSL update of x in place with y = rho.
+constexpr int BK_TILE = 16;
+constexpr int BK_ACHUNK = 12;
+
+__host__ __device__ constexpr int bk_pitch(int MQ) { return MQ | 1; }
+
 template <int MQ, int MODE>
-__global__ void __launch_bounds__(256) k_back(ProjArgs p) {
-  constexpr int VPW = 32 / MQ;
-  const int lane = threadIdx.x & 31;
-  const int sub = lane / MQ;
-  const int q = lane - sub * MQ;
-  if (sub >= VPW) return;
-  const long long vox = ((long long)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5)) * VPW + sub;
-  const long long n_vox = (long long)p.nz * p.ny * p.nx;
-  if (vox >= n_vox) return;
-  const int i = (int)(vox % p.nx);
-  const long long zj = vox / p.nx;
-  const int j = (int)(zj % p.ny);
-  const int z = (int)(zj / p.ny);
+__global__ void __launch_bounds__(BK_TILE * BK_TILE) k_back_tiled(ProjArgs p, int rows_max,
+                                                                   int achunk) {
+  constexpr int PITCH = bk_pitch(MQ);
+  extern __shared__ float4 srho[];           // [achunk][rows_max][PITCH]
+  __shared__ int s_lo[BK_ACHUNK], s_cnt[BK_ACHUNK];
+  const int ntx = (p.nx + BK_TILE - 1) / BK_TILE;
+  const int nty = (p.ny + BK_TILE - 1) / BK_TILE;
+  const int tile = blockIdx.x;
+  const int tx = tile % ntx;
+  const int ty = (tile / ntx) % nty;
+  const int z = tile / (ntx * nty);
+  const int i0 = tx * BK_TILE, j0 = ty * BK_TILE;
+  const int i1 = min(i0 + BK_TILE, p.nx) - 1, j1 = min(j0 + BK_TILE, p.ny) - 1;
+  const int i = i0 + (threadIdx.x % BK_TILE);
+  const int j = j0 + (threadIdx.x / BK_TILE);
+  const bool valid = i < p.nx && j < p.ny;
   const float bc = 0.5f * (float)(p.B - 1);
-  float4 acc = f4(0.f);
+  float4 acc[MQ];
+#pragma unroll
+  for (int q = 0; q < MQ; ++q) acc[q] = f4(0.f);
   float sens = 0.f;
-  for (int ak = 0; ak < p.n_sub; ++ak) {
-    const int a = p.sub[ak];
-    const AngleTab T = p.ang[a];
-    const int n_major = T.xmajor ? p.nx : p.ny;
-    const int n_minor = T.xmajor ? p.ny : p.nx;
-    const int t = T.xmajor ? i : j;
-    const int m = T.xmajor ? j : i;
-    const float tc = 0.5f * (float)(n_major - 1);
-    const float centre = 0.5f * (float)(n_minor - 1);
-    const float inner = inner_pos((float)t - tc, T.gamma, centre);
-    int b_lo, b_hi;
-    bin_range(T, m, inner, bc, p.B, b_lo, b_hi);
-    const float4* yrow = p.y + (size_t)(z * p.n_sub + ak) * p.B * MQ + q;
-    const size_t binrow = (size_t)(z * p.A + a) * p.B;
-    for (int b = b_lo; b <= b_hi; ++b) {
-      const float fr = minor_pos((float)b - bc, T.beta, inner);
-      const float fl = floorf(fr);
-      const int j0 = (int)fl;
-      const float f = fr - fl;
-      float wt = (j0 == m) ? 1.0f - f : ((j0 + 1 == m) ? f : 0.0f);
-      if (wt == 0.0f) continue;
-      wt *= T.w;
-      if (MODE == 1 && p.bin_factor) wt *= __ldg(p.bin_factor + binrow + b);
-      fma4(acc, wt, __ldg(yrow + (size_t)b * MQ));
-      sens += wt;
+  for (int a0 = 0; a0 < p.n_sub; a0 += achunk) {
+    const int na = min(achunk, p.n_sub - a0);
+    if ((int)threadIdx.x < na) {
+      // union of the candidate ranges of the tile's four corners
+      const AngleTab T = p.ang[p.sub[a0 + threadIdx.x]];
+      const int n_major = T.xmajor ? p.nx : p.ny;
+      const int n_minor = T.xmajor ? p.ny : p.nx;
+      const float tc = 0.5f * (float)(n_major - 1);
+      const float centre = 0.5f * (float)(n_minor - 1);
+      const int ta = T.xmajor ? i0 : j0, tb = T.xmajor ? i1 : j1;
+      const int ma = T.xmajor ? j0 : i0, mb = T.xmajor ? j1 : i1;
+      int lo = p.B, hi = -1;
+      for (int c = 0; c < 4; ++c) {
+        const int t = (c & 1) ? tb : ta;
+        const int m = (c & 2) ? mb : ma;
+        int l, h;
+        bin_range(T, m, inner_pos((float)t - tc, T.gamma, centre), bc, p.B, l, h);
+        lo = min(lo, l);
+        hi = max(hi, h);
+      }
+      lo = max(0, lo - 1);
+      hi = min(p.B - 1, hi + 1);
+      s_lo[threadIdx.x] = lo;
+      s_cnt[threadIdx.x] = max(0, min(hi - lo + 1, rows_max));
     }
+    __syncthreads();
+    for (int c = 0; c < na; ++c) {
+      const float4* src = p.y + ((size_t)(z * p.n_sub + a0 + c) * p.B + s_lo[c]) * MQ;
+      float4* dst = srho + (size_t)c * rows_max * PITCH;
+      const int n = s_cnt[c] * MQ;
+      for (int e = threadIdx.x; e < n; e += BK_TILE * BK_TILE) {
+        const int r = e / MQ, q = e - r * MQ;
+        dst[r * PITCH + q] = __ldg(src + e);
+      }
+    }
+    __syncthreads();
+    if (valid) {
+      for (int c = 0; c < na; ++c) {
+        const int a = p.sub[a0 + c];
+        const AngleTab T = p.ang[a];
+        const int n_major = T.xmajor ? p.nx : p.ny;
+        const int n_minor = T.xmajor ? p.ny : p.nx;
+        const int t = T.xmajor ? i : j;
+        const int m = T.xmajor ? j : i;
+        const float tc = 0.5f * (float)(n_major - 1);
+        const float centre = 0.5f * (float)(n_minor - 1);
+        const float inner = inner_pos((float)t - tc, T.gamma, centre);
+        int b_lo, b_hi;
+        bin_range_tight(T, m, inner, bc, p.B, b_lo, b_hi);
+        const int lo = s_lo[c];
+        b_lo = max(b_lo, lo);
+        b_hi = min(b_hi, lo + s_cnt[c] - 1);
+        const float4* rows = srho + (size_t)c * rows_max * PITCH;
+        const size_t binrow = (size_t)(z * p.A + a) * p.B;
+        for (int b = b_lo; b <= b_hi; ++b) {
+          const float fr = minor_pos((float)b - bc, T.beta, inner);
+          const float fl = floorf(fr);
+          const int jj = (int)fl;
+          const float f = fr - fl;
+          float wt = (jj == m) ? 1.0f - f : ((jj + 1 == m) ? f : 0.0f);
+          if (wt == 0.0f) continue;
+          wt *= T.w;
+          if (MODE == 1 && p.bin_factor) wt *= __ldg(p.bin_factor + binrow + b);
+          const float4* row = rows + (b - lo) * PITCH;
+#pragma unroll
+          for (int q = 0; q < MQ; ++q) fma4(acc[q], wt, row[q]);
+          sens += wt;
+        }
+      }
+    }
+    __syncthreads();
   }
-  const size_t vi = (size_t)vox * MQ + q;
+  if (!valid) return;
+  const size_t vi = ((size_t)(z * p.ny + j) * p.nx + i) * MQ;
   if (MODE == 0) {
-    p.xout[vi] = acc;
+#pragma unroll
+    for (int q = 0; q < MQ; ++q) p.xout[vi + q] = acc[q];
     return;
   }
-  float4 xv = p.x[vi];
-  if (sens > 0.f) {
+  if (!(sens > 0.f)) return;   // x unchanged where no ray of the subset sees the voxel
+  const float ks = p.kappa * sens;
+#pragma unroll
+  for (int q = 0; q < MQ; ++q) {
+    float4 xv = p.x[vi + q];
     const float4 dt = __ldg(p.dt + q);
-    const float ks = p.kappa * sens;
     float4 den = make_float4(dt.x * ks, dt.y * ks, dt.z * ks, dt.w * ks);
     if (p.F) {
-      const float4 Fv = __ldg(p.F + vi);
+      const float4 Fv = __ldg(p.F + vi + q);
       const float ps = p.prior_scale;
       den.x = fmaxf(fmaf(ps, xv.x - Fv.x, den.x), 1e-3f * den.x);
       den.y = fmaxf(fmaf(ps, xv.y - Fv.y, den.y), 1e-3f * den.y);
       den.z = fmaxf(fmaf(ps, xv.z - Fv.z, den.z), 1e-3f * den.z);
       den.w = fmaxf(fmaf(ps, xv.w - Fv.w, den.w), 1e-3f * den.w);
     }
-    xv.x = xv.x * (p.kappa * dt.x * acc.x) / den.x;
-    xv.y = xv.y * (p.kappa * dt.y * acc.y) / den.y;
-    xv.z = xv.z * (p.kappa * dt.z * acc.z) / den.z;
-    xv.w = xv.w * (p.kappa * dt.w * acc.w) / den.w;
+    xv.x = xv.x * (p.kappa * dt.x * acc[q].x) / den.x;
+    xv.y = xv.y * (p.kappa * dt.y * acc[q].y) / den.y;
+    xv.z = xv.z * (p.kappa * dt.z * acc[q].z) / den.z;
+    xv.w = xv.w * (p.kappa * dt.w * acc[q].w) / den.w;
+    p.xout[vi + q] = xv;
   }
-  p.xout[vi] = xv;
 }
 
 // Sensitivity sum_{d in S_k} n_d p_vd: the same gather with unit data.
@@ -247,7 +326,7 @@ __global__ void __launch_bounds__(256) k_sens(ProjArgs p, float* sens_out) {
     const float centre = 0.5f * (float)(n_minor - 1);
     const float inner = inner_pos((float)t - tc, T.gamma, centre);
     int b_lo, b_hi;
-    bin_range(T, m, inner, bc, p.B, b_lo, b_hi);
+    bin_range_tight(T, m, inner, bc, p.B, b_lo, b_hi);
     const size_t binrow = (size_t)(z * p.A + a) * p.B;
     for (int b = b_lo; b <= b_hi; ++b) {
       const float fr = minor_pos((float)b - bc, T.beta, inner);
@@ -350,22 +429,43 @@ static void launch_forward(int MQ, const ProjArgs& p, cudaStream_t s) {
   }
 }
 
+// Rows of one angle a 16 x 16 tile can touch: the candidate span over the tile
+// (15 steps along both axes plus the +-1 interpolation band) divided by the
+// smallest |beta| (= bin / vox), plus the margins of bin_range and the union.
+static int back_rows_max(const kcs_geometry* g) {
+  const double span = (BK_TILE - 1) * 2.0 + 2.0;
+  return (int)std::ceil(span * g->vox / g->bin) + 8;
+}
+
+constexpr size_t BK_SMEM_MAX = 200 * 1024;   // dynamic shared memory budget per block
+
+template <int MQ, int MODE>
+static int launch_back_mq(const ProjArgs& p, int rows_max, cudaStream_t s) {
+  const size_t row_bytes = sizeof(float4) * rows_max * bk_pitch(MQ);
+  const int achunk = (int)std::min<size_t>(BK_ACHUNK, BK_SMEM_MAX / row_bytes);
+  KCS_REQUIRE(achunk >= 1, "bins are too fine relative to voxels for the tiled back-projection");
+  const size_t smem = row_bytes * achunk;
+  KCS_CUDA(cudaFuncSetAttribute(k_back_tiled<MQ, MODE>,
+                                cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  const long long tiles = (long long)((p.nx + BK_TILE - 1) / BK_TILE) *
+                          ((p.ny + BK_TILE - 1) / BK_TILE) * p.nz;
+  k_back_tiled<MQ, MODE><<<(unsigned)tiles, BK_TILE * BK_TILE, smem, s>>>(p, rows_max, achunk);
+  return KCS_OK;
+}
+
 template <int MODE>
-static void launch_back(int MQ, const ProjArgs& p, cudaStream_t s) {
-  const int vpw = 32 / MQ;
-  const long long vox = (long long)p.nz * p.ny * p.nx;
-  const long long warps = (vox + vpw - 1) / vpw;
-  const unsigned blocks = (unsigned)((warps + 7) / 8);
+static int launch_back(int MQ, const ProjArgs& p, int rows_max, cudaStream_t s) {
   switch (MQ) {
-    case 1: k_back<1, MODE><<<blocks, 256, 0, s>>>(p); break;
-    case 2: k_back<2, MODE><<<blocks, 256, 0, s>>>(p); break;
-    case 3: k_back<3, MODE><<<blocks, 256, 0, s>>>(p); break;
-    case 4: k_back<4, MODE><<<blocks, 256, 0, s>>>(p); break;
-    case 5: k_back<5, MODE><<<blocks, 256, 0, s>>>(p); break;
-    case 6: k_back<6, MODE><<<blocks, 256, 0, s>>>(p); break;
-    case 7: k_back<7, MODE><<<blocks, 256, 0, s>>>(p); break;
-    case 8: k_back<8, MODE><<<blocks, 256, 0, s>>>(p); break;
+    case 1: return launch_back_mq<1, MODE>(p, rows_max, s);
+    case 2: return launch_back_mq<2, MODE>(p, rows_max, s);
+    case 3: return launch_back_mq<3, MODE>(p, rows_max, s);
+    case 4: return launch_back_mq<4, MODE>(p, rows_max, s);
+    case 5: return launch_back_mq<5, MODE>(p, rows_max, s);
+    case 6: return launch_back_mq<6, MODE>(p, rows_max, s);
+    case 7: return launch_back_mq<7, MODE>(p, rows_max, s);
+    case 8: return launch_back_mq<8, MODE>(p, rows_max, s);
   }
+  return KCS_ERR_INVALID_ARG;
 }
 
 }  // namespace kcs
@@ -399,11 +499,14 @@ int kcs_create_geometry(kcs_geometry_t** out, int nx, int ny, int nz, float vox_
       T.beta = (float)(bin_mm / (s * vox_mm));
       T.gamma = (float)(-c / s);
       T.w = (float)(vox_mm / fabs(s));
+      T.inv_beta = (float)(s * vox_mm / bin_mm);
     } else {
       T.beta = (float)(bin_mm / (c * vox_mm));
       T.gamma = (float)(-s / c);
       T.w = (float)(vox_mm / fabs(c));
+      T.inv_beta = (float)(c * vox_mm / bin_mm);
     }
+    T.pad[0] = T.pad[1] = T.pad[2] = 0.f;
     tab[a] = T;
   }
   kcs_geometry* g = new kcs_geometry();
@@ -485,7 +588,8 @@ int kcs_back_project(const kcs_geometry_t* g, int subset, int n_frames, const fl
   ProjArgs p = base_args(g, subset);
   p.y = reinterpret_cast<const float4*>(y);
   p.xout = reinterpret_cast<float4*>(x);
-  launch_back<0>(n_frames / 4, p, as_stream(stream));
+  st = launch_back<0>(n_frames / 4, p, back_rows_max(g), as_stream(stream));
+  if (st) return st;
   KCS_LAUNCHED();
   return KCS_OK;
 }
@@ -563,7 +667,8 @@ int kcs_osl_backproject(const kcs_geometry_t* g, int subset, int n_frames, const
   q.kappa = kappa;
   q.F = (F_model && beta_kp != 0.f) ? reinterpret_cast<const float4*>(F_model) : nullptr;
   q.prior_scale = q.F ? beta_kp / ((float)g->S * sigma2) : 0.f;
-  launch_back<1>(n_frames / 4, q, as_stream(stream));
+  st = launch_back<1>(n_frames / 4, q, back_rows_max(g), as_stream(stream));
+  if (st) return st;
   KCS_LAUNCHED();
   return KCS_OK;
 }
