@@ -361,8 +361,14 @@ __global__ void k_huber_grad(int nx, int ny, int nz, const float* p, float delta
 }
 
 // ---------------------------------------------------------------- MAP-LM
+#ifndef KCS_LM_VPT
+#define KCS_LM_VPT 1
+#endif
+#ifndef KCS_LM_MINBLOCKS
+#define KCS_LM_MINBLOCKS 8
+#endif
 constexpr int LM_THREADS = 128;
-constexpr int LM_VPT = 2;                       // voxels per thread
+constexpr int LM_VPT = KCS_LM_VPT;              // voxels per thread
 constexpr int LM_BLOCK_VOX = LM_THREADS * LM_VPT;
 __constant__ float c_lo[4] = {0.f, 0.f, 0.f, 0.f};
 __constant__ float c_hi[4] = {2.f, 2.f, 1.f, 1.f};
@@ -473,7 +479,7 @@ __device__ __forceinline__ void huber_terms(const LmArgs& L, long long V, long l
     }
 }
 
-__global__ void __launch_bounds__(LM_THREADS, 4) k_lm_step(LmArgs L) {
+__global__ void __launch_bounds__(LM_THREADS, KCS_LM_MINBLOCKS) k_lm_step(LmArgs L) {
   extern __shared__ float xs_all[];
   const int M = L.kd.M;
   const int ld = M + 1;
