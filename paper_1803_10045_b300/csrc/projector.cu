@@ -106,16 +106,34 @@ __global__ void __launch_bounds__(256) k_forward(ProjArgs p) {
     t0 = max(0, (int)floorf(fmaxf(lo, -4.0f)) - 2);
     t1 = min(n_major - 1, (int)ceilf(fminf(hi, (float)n_major + 4.0f)) + 2);
   }
+  // Branch-free march, 4 steps per trip: out-of-grid partners are predicated
+  // loads of zero (their weight is exactly 0), so several steps' loads are in
+  // flight at once and the accumulated values equal the plain loop's.
   float4 acc = f4(0.f);
-  for (int t = t0; t <= t1; ++t) {
-    const float fr = minor_pos(bf, T.beta, inner_pos((float)t - tc, T.gamma, centre));
-    const float fl = floorf(fr);
-    const int j0 = (int)fl;
-    if (j0 < -1 || j0 >= n_minor) continue;
-    const float f = fr - fl;
-    const float4* px = xz + (size_t)t * s_major + (ptrdiff_t)j0 * s_minor;
-    if (j0 >= 0) fma4(acc, 1.0f - f, __ldg(px));
-    if (j0 + 1 < n_minor) fma4(acc, f, __ldg(px + s_minor));
+  constexpr int U = 4;
+  for (int tb = t0; tb <= t1; tb += U) {
+    float4 v0[U], v1[U];
+    float w0[U], w1[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int t = tb + u;
+      const float fr = minor_pos(bf, T.beta, inner_pos((float)t - tc, T.gamma, centre));
+      const float fl = floorf(fr);
+      const int j0 = (int)fl;
+      const float f = fr - fl;
+      const bool in0 = t <= t1 && j0 >= 0 && j0 < n_minor;
+      const bool in1 = t <= t1 && j0 >= -1 && j0 + 1 < n_minor;
+      const float4* px = xz + (ptrdiff_t)t * s_major + (ptrdiff_t)j0 * s_minor;
+      v0[u] = in0 ? __ldg(px) : f4(0.f);
+      v1[u] = in1 ? __ldg(px + s_minor) : f4(0.f);
+      w0[u] = in0 ? 1.0f - f : 0.f;
+      w1[u] = in1 ? f : 0.f;
+    }
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      fma4(acc, w0[u], v0[u]);
+      fma4(acc, w1[u], v1[u]);
+    }
   }
   acc.x *= T.w; acc.y *= T.w; acc.z *= T.w; acc.w *= T.w;
   const size_t oi = ((size_t)(z * p.n_sub + ak) * p.B + b) * MQ + q;
@@ -185,7 +203,8 @@ __global__ void __launch_bounds__(BK_TILE * BK_TILE) k_back_tiled(ProjArgs p, in
                                                                    int achunk) {
   constexpr int PITCH = bk_pitch(MQ);
   extern __shared__ float4 srho[];           // [achunk][rows_max][PITCH]
-  __shared__ int s_lo[BK_ACHUNK], s_cnt[BK_ACHUNK];
+  __shared__ int s_lo[BK_ACHUNK], s_cnt[BK_ACHUNK], s_a[BK_ACHUNK];
+  __shared__ AngleTab s_T[BK_ACHUNK];
   const int ntx = (p.nx + BK_TILE - 1) / BK_TILE;
   const int nty = (p.ny + BK_TILE - 1) / BK_TILE;
   const int tile = blockIdx.x;
@@ -206,7 +225,10 @@ __global__ void __launch_bounds__(BK_TILE * BK_TILE) k_back_tiled(ProjArgs p, in
     const int na = min(achunk, p.n_sub - a0);
     if ((int)threadIdx.x < na) {
       // union of the candidate ranges of the tile's four corners
-      const AngleTab T = p.ang[p.sub[a0 + threadIdx.x]];
+      const int a = p.sub[a0 + threadIdx.x];
+      const AngleTab T = p.ang[a];
+      s_a[threadIdx.x] = a;
+      s_T[threadIdx.x] = T;
       const int n_major = T.xmajor ? p.nx : p.ny;
       const int n_minor = T.xmajor ? p.ny : p.nx;
       const float tc = 0.5f * (float)(n_major - 1);
@@ -240,8 +262,8 @@ __global__ void __launch_bounds__(BK_TILE * BK_TILE) k_back_tiled(ProjArgs p, in
     __syncthreads();
     if (valid) {
       for (int c = 0; c < na; ++c) {
-        const int a = p.sub[a0 + c];
-        const AngleTab T = p.ang[a];
+        const int a = s_a[c];
+        const AngleTab T = s_T[c];
         const int n_major = T.xmajor ? p.nx : p.ny;
         const int n_minor = T.xmajor ? p.ny : p.nx;
         const int t = T.xmajor ? i : j;
