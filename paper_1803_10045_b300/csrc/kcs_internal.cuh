@@ -97,8 +97,16 @@ constexpr float DCENT = 0.25f;
 constexpr int NCH = 12;         // channels per term, padded to 3 float4
 constexpr double DT_MAX = 5.0;  // longest propagation interval (min)
 
-// Channel order inside a term's 12 floats.
+// Channel numbering of the float64 base series.
 enum { CH_M1 = 0, CH_G, CH_M2, CH_H, CH_M3, CH_D1, CH_GP, CH_D2, CH_HP, CH_D3 };
+// Packing of a term's channels into 3 float4 parts: part 0 (m1, m2, m3, d1) and
+// part 1 (d2, d3, -, -) depend on the input over the interval; part 2
+// (g, h, gp, hp) only on a and D, so it is evaluated once per distinct D.
+__host__ __device__ constexpr int ch_slot(int ch) {
+  return ch == CH_M1 ? 0 : ch == CH_M2 ? 1 : ch == CH_M3 ? 2 : ch == CH_D1 ? 3
+       : ch == CH_D2 ? 4 : ch == CH_D3 ? 5
+       : ch == CH_G ? 8 : ch == CH_H ? 9 : ch == CH_GP ? 10 : 11;   // CH_HP
+}
 
 struct KinDev {
   const float4* coef;   // [n_iv][KC][3][NCENT] float4 (12 channels = 3 parts)

@@ -123,10 +123,11 @@ __global__ void k_shift(const double* base, float* coef) {
     r *= a0 * (double)(j + m + 1) / (double)(m + 1);
   }
   float* o = coef + (((size_t)iv * KC + j) * 3 * NCENT) * 4;   // [iv][j][part][centre][4]
-  o[((ch / 4) * NCENT + c) * 4 + ch % 4] = (float)sum;
+  const int slot = ch_slot(ch);
+  o[((slot / 4) * NCENT + c) * 4 + slot % 4] = (float)sum;
   if (ch == 0) {
-    o[(2 * NCENT + c) * 4 + 2] = 0.f;
-    o[(2 * NCENT + c) * 4 + 3] = 0.f;
+    o[(1 * NCENT + c) * 4 + 2] = 0.f;
+    o[(1 * NCENT + c) * 4 + 3] = 0.f;
   }
 }
 
@@ -150,10 +151,10 @@ __device__ __forceinline__ int series_terms(float y) {
   return (int)ceilf(fmaf(2.0f, y, fmaf(5.75f, sqrtf(y), 3.75f)));
 }
 
-// Horner evaluation of the 5 value channels (and the 5 derivative channels when
-// JAC) of one voxel from a table row set tab (KC terms x 3 float4) at delta.
+// Input-driven series values of one voxel and interval (the derivative
+// channels d1..d3 only when the Jacobian is wanted).
 struct Series {
-  float m1, g, m2, h, m3, d1, gp, d2, hp, d3;
+  float m1, m2, m3, d1, d2, d3;
 };
 
 // Evaluates F_m (and dF_m/d(K1,k2,k3,Vb) when JAC) of VPT voxels frame by frame
@@ -173,39 +174,62 @@ __device__ __forceinline__ void eval_model(const KinDev& kd, const float (&K1)[V
     cen[v] = min(NCENT - 1, (int)(a[v] * (1.0f / DCENT)));
     dl[v] = a[v] - (float)cen[v] * DCENT;
   }
+  // Frame schedules repeat interval lengths (PR2: 4 distinct over 24 intervals),
+  // so the series length, e^{-aD} and the input-free terms G, H (and their
+  // a-derivatives) are recomputed only when D changes.
+  float Dprev = -1.f, E[VPT], Gc[VPT], Hc[VPT], Gpc[VPT], Hpc[VPT];
+  int K = 0;
   for (int iv = 0; iv < kd.n_iv; ++iv) {
     const float D = __ldg(kd.iv_dt + iv);
-    int K = 0;
-#pragma unroll
-    for (int v = 0; v < VPT; ++v) K = max(K, series_terms(dl[v] * D));
-    K = min(KC, __reduce_max_sync(mask, K));   // one trip count per warp
     const float4* tab = kd.coef + (size_t)iv * KC * 3 * NCENT;
+    if (D != Dprev) {   // uniform across the warp
+      Dprev = D;
+      K = 0;
+#pragma unroll
+      for (int v = 0; v < VPT; ++v) {
+        K = max(K, series_terms(dl[v] * D));
+        E[v] = expf(-a[v] * D);
+      }
+      K = min(KC, __reduce_max_sync(mask, K));   // one trip count per warp
+#pragma unroll
+      for (int v = 0; v < VPT; ++v) {
+        float g = 0.f, h = 0.f, gp = 0.f, hp = 0.f;
+        for (int n = K - 1; n >= 0; --n) {
+          const float4 c = __ldg(tab + (size_t)n * 3 * NCENT + 2 * NCENT + cen[v]);
+          g = fmaf(g, dl[v], c.x);
+          h = fmaf(h, dl[v], c.y);
+          if (JAC) {
+            gp = fmaf(gp, dl[v], c.z);
+            hp = fmaf(hp, dl[v], c.w);
+          }
+        }
+        Gc[v] = E[v] * g;
+        Hc[v] = E[v] * h;
+        Gpc[v] = -E[v] * gp;
+        Hpc[v] = -E[v] * hp;
+      }
+    }
     Series p[VPT];
 #pragma unroll
-    for (int v = 0; v < VPT; ++v) p[v] = Series{0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+    for (int v = 0; v < VPT; ++v) p[v] = Series{0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
 #pragma unroll 2
     for (int n = K - 1; n >= 0; --n) {
       const float4* row = tab + (size_t)n * 3 * NCENT;
-      float4 c0, c1, c2;
+      float4 c0, c1;
 #pragma unroll
       for (int v = 0; v < VPT; ++v) {
         if (v == 0 || cen[v] != cen[v - 1]) {   // the voxels of a thread often share a centre
           c0 = __ldg(row + cen[v]);
-          c1 = __ldg(row + NCENT + cen[v]);
-          c2 = JAC ? __ldg(row + 2 * NCENT + cen[v]) : make_float4(0.f, 0.f, 0.f, 0.f);
+          c1 = JAC ? __ldg(row + NCENT + cen[v]) : make_float4(0.f, 0.f, 0.f, 0.f);
         }
         const float d = dl[v];
         p[v].m1 = fmaf(p[v].m1, d, c0.x);
-        p[v].g = fmaf(p[v].g, d, c0.y);
-        p[v].m2 = fmaf(p[v].m2, d, c0.z);
-        p[v].h = fmaf(p[v].h, d, c0.w);
-        p[v].m3 = fmaf(p[v].m3, d, c1.x);
+        p[v].m2 = fmaf(p[v].m2, d, c0.y);
+        p[v].m3 = fmaf(p[v].m3, d, c0.z);
         if (JAC) {
-          p[v].d1 = fmaf(p[v].d1, d, c1.y);
-          p[v].gp = fmaf(p[v].gp, d, c1.z);
-          p[v].d2 = fmaf(p[v].d2, d, c1.w);
-          p[v].hp = fmaf(p[v].hp, d, c2.x);
-          p[v].d3 = fmaf(p[v].d3, d, c2.y);
+          p[v].d1 = fmaf(p[v].d1, d, c0.w);
+          p[v].d2 = fmaf(p[v].d2, d, c1.x);
+          p[v].d3 = fmaf(p[v].d3, d, c1.y);
         }
       }
     }
@@ -217,22 +241,22 @@ __device__ __forceinline__ void eval_model(const KinDev& kd, const float (&K1)[V
     const float cpf = frame_end ? __ldg(kd.fr_cp + m) : 0.f;
 #pragma unroll
     for (int v = 0; v < VPT; ++v) {
-      const float E = expf(-a[v] * D);
-      const float G = E * p[v].g, H = E * p[v].h;
-      const float A = fmaf(I[v], G, E * p[v].m2);
-      const float B = fmaf(Jr[v], D, fmaf(I[v], H, E * p[v].m3));
+      const float Ev = E[v];
+      const float G = Gc[v], H = Hc[v];
+      const float A = fmaf(I[v], G, Ev * p[v].m2);
+      const float B = fmaf(Jr[v], D, fmaf(I[v], H, Ev * p[v].m3));
       if (JAC) {
-        const float Gp = -E * p[v].gp, Hp = -E * p[v].hp;
-        const float Ap = fmaf(Ip[v], G, fmaf(I[v], Gp, -E * p[v].d2));
-        const float Bp = fmaf(Jp[v], D, fmaf(Ip[v], H, fmaf(I[v], Hp, -E * p[v].d3)));
-        Ip[v] = fmaf(E, fmaf(-D, I[v], Ip[v]), -E * p[v].d1);
+        const float Gp = Gpc[v], Hp = Hpc[v];
+        const float Ap = fmaf(Ip[v], G, fmaf(I[v], Gp, -Ev * p[v].d2));
+        const float Bp = fmaf(Jp[v], D, fmaf(Ip[v], H, fmaf(I[v], Hp, -Ev * p[v].d3)));
+        Ip[v] = fmaf(Ev, fmaf(-D, I[v], Ip[v]), -Ev * p[v].d1);
         Jp[v] += Ap;
         if (in_frame) {
           SAp[v] += Ap;
           SBp[v] += Bp;
         }
       }
-      I[v] = fmaf(E, I[v], E * p[v].m1);
+      I[v] = fmaf(Ev, I[v], Ev * p[v].m1);
       Jr[v] += A;
       if (in_frame) {
         SA[v] += A;
@@ -427,26 +451,37 @@ struct DeltaSink {
   }
 };
 
+// 1/sqrt(d) in float64 for 1e-30 < d < 1e30: float32 seed, then one
+// Newton-Raphson step r <- r (3 - d r^2) / 2, which squares the seed's relative
+// error (~1e-7 -> ~1e-14).
+__device__ __forceinline__ double rsqrt_nr(double d) {
+  const double r = (double)rsqrtf((float)d);
+  return r * fma(-0.5 * d, r * r, 1.5);
+}
+
 // Cholesky solve of the damped 4x4 normal equations in float64.  Returns
 // false (no step) if a pivot is not positive.
 __device__ bool solve4(const Normal& s, double lam, const double rhs[4], double out[4]) {
   const double A00 = (double)s.A00 + lam, A11 = (double)s.A11 + lam, A22 = (double)s.A22 + lam,
                A33 = (double)s.A33 + lam;
   const double A10 = s.A01, A20 = s.A02, A30 = s.A03, A21 = s.A12, A31 = s.A13, A32 = s.A23;
-  if (!(A00 > 0.0)) return false;
-  const double i0 = rsqrt(A00);
+  // pivots never exceed their diagonal entry, so bounding the diagonal keeps
+  // every pivot inside the float32 seed's range
+  if (!(A00 < 1e30 && A11 < 1e30 && A22 < 1e30 && A33 < 1e30)) return false;
+  if (!(A00 > 1e-30)) return false;
+  const double i0 = rsqrt_nr(A00);
   const double L10 = A10 * i0, L20 = A20 * i0, L30 = A30 * i0;
   const double d1 = A11 - L10 * L10;
-  if (!(d1 > 0.0)) return false;
-  const double i1 = rsqrt(d1);
+  if (!(d1 > 1e-30)) return false;
+  const double i1 = rsqrt_nr(d1);
   const double L21 = (A21 - L20 * L10) * i1, L31 = (A31 - L30 * L10) * i1;
   const double d2 = A22 - L20 * L20 - L21 * L21;
-  if (!(d2 > 0.0)) return false;
-  const double i2 = rsqrt(d2);
+  if (!(d2 > 1e-30)) return false;
+  const double i2 = rsqrt_nr(d2);
   const double L32 = (A32 - L30 * L20 - L31 * L21) * i2;
   const double d3 = A33 - L30 * L30 - L31 * L31 - L32 * L32;
-  if (!(d3 > 0.0)) return false;
-  const double i3 = rsqrt(d3);
+  if (!(d3 > 1e-30)) return false;
+  const double i3 = rsqrt_nr(d3);
   const double z0 = rhs[0] * i0;
   const double z1 = (rhs[1] - L10 * z0) * i1;
   const double z2 = (rhs[2] - L20 * z0 - L21 * z1) * i2;
