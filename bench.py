@@ -54,6 +54,28 @@ FP32_LANES_PER_SM, N_SM = 128, 148
 LM_FLOPS_PER_VOXEL_STEP = 2 * 15 * 330 + 24 * (2 * 25 + 2 * 15) + 400
 
 
+# DRAM traffic (read + write) per launch measured by ncu on the 16-central-plane
+# case of this workload and scaled by 127/16 (traffic grows with the number of
+# planes: every kernel touches each plane's data independently), valid while
+# the kernel's source file is unchanged (sha256 prefix); see profiles/.
+TRAFFIC = {
+    "lm_step": {"bytes": 247.36e6 * 127 / 16, "src": "kinetics.cu", "sha": "cd58f0be38e22b87"},
+    "bwd_osl": {"bytes": 505.94e6 * 127 / 16, "src": "projector.cu", "sha": "66b4b2a2b0f15b26"},
+    "fwd_ratio": {"bytes": 237.46e6 * 127 / 16, "src": "projector.cu", "sha": "66b4b2a2b0f15b26"},
+}
+
+
+def _traffic(kernel):
+    import hashlib
+    t = TRAFFIC.get(kernel)
+    if not t:
+        return None
+    path = os.path.join(ROOT, "paper_1803_10045_b300", "csrc", t["src"])
+    with open(path, "rb") as f:
+        sha = hashlib.sha256(f.read()).hexdigest()[:16]
+    return round(t["bytes"] / 1e9, 4) if sha == t["sha"] else None
+
+
 def _peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -331,19 +353,23 @@ def run_ours(args):
         avg = sum(ts_) / launches
         kernels[name] = {"launches": launches, "avg_ms": round(avg, 4),
                          "share": round(sum(ts_) / total_ms, 4),
-                         "alg_GBps": round(alg[name] / (avg * 1e-3) / 1e9, 1)}
+                         "alg_GB": round(alg[name] / 1e9, 4),
+                         "alg_GBps": round(alg[name] / (avg * 1e-3) / 1e9, 1),
+                         "frac_hbm": round(alg[name] / (avg * 1e-3) / 1e9 / hbm, 4),
+                         "traffic_GB": _traffic(name)}
     dom = max(kernels, key=lambda n: kernels[n]["share"])
     fp32_peak = N_SM * FP32_LANES_PER_SM * 2 * smax * 1e6 / 1e12
     if dom == "lm_step":
         ach = V * LM_FLOPS_PER_VOXEL_STEP / (kernels[dom]["avg_ms"] * 1e-3) / 1e12
         roof = {"bound": "alu", "kernel": dom, "achieved": round(ach, 2),
                 "peak": round(fp32_peak, 1), "unit": "TFLOP/s", "frac": round(ach / fp32_peak, 4),
-                "traffic": None,
+                "traffic": _traffic(dom), "traffic_unit": "GB/launch",
                 "peak_source": f"FP32 FMA {N_SM} SM x {FP32_LANES_PER_SM} lanes x 2 x {smax:.0f} MHz"}
     else:
         ach = kernels[dom]["alg_GBps"]
         roof = {"bound": "hbm", "kernel": dom, "achieved": ach, "peak": hbm, "unit": "GB/s",
-                "frac": round(ach / hbm, 4), "traffic": None, "peak_source": f"{src} hbm_gbs"}
+                "frac": round(ach / hbm, 4), "traffic": _traffic(dom), "traffic_unit": "GB/launch",
+                "peak_source": f"{src} hbm_gbs"}
     lm_ms = kernels["lm_step"]["avg_ms"]
     out = {
         "metric": METRIC, "value": round(value, 4), "unit": "iter/s", "n_gpus": world,
