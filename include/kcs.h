@@ -152,6 +152,12 @@ int kcs_destroy_kinetics(kcs_kinetics_t* k);
  * J [n_vox][M][4] (d/dK1, d/dk2, d/dk3, d/dVb) when not NULL. */
 int kcs_tac_eval(const kcs_kinetics_t* k, int64_t n_vox, const float* params, float* F,
                  float* J, void* stream);
+/* Reverse mode of kcs_tac_eval: gparams[q][v] = sum_m dF_vm/dxi_q * gF[v][m]
+ * (the analytic kinetic Jacobian of Sec. II-C transposed), for differentiating
+ * y = P F(params) by composing with kcs_back_project.  params [4][n_vox],
+ * gF [n_vox][M] -> gparams [4][n_vox] (overwritten). */
+int kcs_tac_vjp(const kcs_kinetics_t* k, int64_t n_vox, const float* params, const float* gF,
+                float* gparams, void* stream);
 /* Ki = K1 k3 / (k2 + k3) (0 where k2 + k3 = 0), Sec. IV-B: [4][n_vox] -> [n_vox]. */
 int kcs_ki(int64_t n_vox, const float* params, float* ki, void* stream);
 

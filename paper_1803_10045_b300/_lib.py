@@ -62,6 +62,7 @@ SIGNATURES = {
     "kcs_destroy_kinetics": (i32, [vp]),
     "kcs_tac_eval": (i32, [vp, i64, vp, vp, vp, vp]),
     "kcs_ki": (i32, [i64, vp, vp, vp]),
+    "kcs_tac_vjp": (i32, [vp, i64, vp, vp, vp, vp]),
     "kcs_huber_grad": (i32, [i32, i32, i32, vp, f32, vp, vp]),
     "kcs_lm_workspace_size": (sz, [i32, i32, i32]),
     "kcs_map_lm_fit": (i32, [vp, i32, i32, i32, vp, vp, vp, i32, f32, f32, vp, vp, sz, vp]),

@@ -350,6 +350,46 @@ int launch_tac_eval(const kcs_kinetics* k, int64_t n_vox, const float* params, f
   return KCS_OK;
 }
 
+// ---------------------------------------------------------------- tac_vjp
+// gparams[q][v] = sum_m dF_vm/dxi_q gF_vm: the kinetic Jacobian transposed,
+// applied to a gradient with respect to the model TACs (reverse mode of
+// kcs_tac_eval).
+struct VjpSink {
+  const float* g;   // this voxel's gF row in shared memory
+  float acc[4];
+  __device__ void operator()(int, int m, float, float j0, float j1, float j2, float j3) {
+    const float gm = g[m];
+    acc[0] = fmaf(j0, gm, acc[0]);
+    acc[1] = fmaf(j1, gm, acc[1]);
+    acc[2] = fmaf(j2, gm, acc[2]);
+    acc[3] = fmaf(j3, gm, acc[3]);
+  }
+};
+
+__global__ void __launch_bounds__(TAC_THREADS) k_tac_vjp(KinDev kd, long long n_vox,
+                                                         const float* __restrict__ params,
+                                                         const float* __restrict__ gF,
+                                                         float* __restrict__ gparams) {
+  extern __shared__ float sg[];
+  const int M = kd.M;
+  const int ld = M + 1;
+  const long long v0 = (long long)blockIdx.x * TAC_THREADS;
+  const long long v = v0 + threadIdx.x;
+  const long long nv = min((long long)TAC_THREADS, n_vox - v0);
+  for (long long e = threadIdx.x; e < nv * M; e += TAC_THREADS) {
+    const long long r = e / M, m = e - r * M;
+    sg[r * ld + m] = gF[v0 * M + e];
+  }
+  __syncthreads();
+  if (v >= n_vox) return;
+  const float K1[1] = {params[v]}, k2[1] = {params[n_vox + v]}, k3[1] = {params[2 * n_vox + v]},
+              Vb[1] = {params[3 * n_vox + v]};
+  VjpSink sink{sg + threadIdx.x * ld, {0.f, 0.f, 0.f, 0.f}};
+  eval_model<1, true>(kd, K1, k2, k3, Vb, sink);
+#pragma unroll
+  for (int q = 0; q < 4; ++q) gparams[q * n_vox + v] = sink.acc[q];
+}
+
 // ---------------------------------------------------------------- Ki
 __global__ void k_ki(long long n, const float* p, float* ki) {
   const long long v = (long long)blockIdx.x * blockDim.x + threadIdx.x;
@@ -733,6 +773,19 @@ int kcs_tac_eval(const kcs_kinetics_t* k, int64_t n_vox, const float* params, fl
   KCS_REQUIRE(k && params && F, "NULL argument");
   KCS_REQUIRE(n_vox >= 0, "n_vox < 0");
   return launch_tac_eval(k, n_vox, params, F, J, as_stream(stream));
+}
+
+int kcs_tac_vjp(const kcs_kinetics_t* k, int64_t n_vox, const float* params, const float* gF,
+                float* gparams, void* stream) {
+  clear_error();
+  KCS_REQUIRE(k && params && gF && gparams, "NULL argument");
+  KCS_REQUIRE(n_vox >= 0, "n_vox < 0");
+  if (n_vox == 0) return KCS_OK;
+  const size_t smem = sizeof(float) * TAC_THREADS * (k->M + 1);
+  k_tac_vjp<<<(unsigned)((n_vox + TAC_THREADS - 1) / TAC_THREADS), TAC_THREADS, smem,
+              as_stream(stream)>>>(k->dev(), n_vox, params, gF, gparams);
+  KCS_LAUNCHED();
+  return KCS_OK;
 }
 
 int kcs_ki(int64_t n_vox, const float* params, float* ki, void* stream) {
