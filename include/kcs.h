@@ -61,6 +61,19 @@ enum kcs_randoms_layout {
   KCS_RANDOMS_FULL = 2       /* float [Z][A][B][M]                       */
 };
 
+/* Storage type of an image / ratio sinogram (KCS_F32, KCS_BF16, KCS_F16) or of
+ * the counts (KCS_F32, KCS_U16) in the *_ex entry points (the precision form).
+ * Arithmetic is float32 whatever the storage; a stored image holds x / scale_m
+ * with a caller-chosen per-frame scale [M] (device; NULL = 1); a 16-bit image
+ * or ratio array must be 8-byte aligned.  Half-precision stores saturate at
+ * 65504 instead of overflowing. */
+enum kcs_storage {
+  KCS_F32 = 0,
+  KCS_BF16 = 1,
+  KCS_F16 = 2,
+  KCS_U16 = 3
+};
+
 /* Thread-local description of the last failure on this thread ("" if none). */
 const char* kcs_last_error(void);
 /* ABI version, incremented on any incompatible change. */
@@ -125,6 +138,22 @@ int kcs_osl_backproject(const kcs_geometry_t* g, int subset, int n_frames, const
                         float kappa, const float* bin_factor, const float* rho,
                         const float* F_model, float beta_kp, float sigma2, float* x,
                         void* stream);
+/* Precision form of the three calls above: counts stored as counts_type, the
+ * image x as x_type with per-frame scale x_scale, and the ratio rho (or the
+ * workspace holding it) stored as x_type; projections and updates are float32. */
+int kcs_osl_ratio_ex(const kcs_geometry_t* g, int subset, int n_frames, const float* frame_dt,
+                     float kappa, const void* counts, int counts_type, const float* randoms,
+                     int randoms_layout, const float* bin_factor, const void* x, int x_type,
+                     const float* x_scale, void* rho, void* stream);
+int kcs_osl_backproject_ex(const kcs_geometry_t* g, int subset, int n_frames,
+                           const float* frame_dt, float kappa, const float* bin_factor,
+                           const void* rho, const float* F_model, float beta_kp, float sigma2,
+                           void* x, int x_type, const float* x_scale, void* stream);
+int kcs_osl_update_ex(const kcs_geometry_t* g, int subset, int n_frames, const float* frame_dt,
+                      float kappa, const void* counts, int counts_type, const float* randoms,
+                      int randoms_layout, const float* bin_factor, const float* F_model,
+                      float beta_kp, float sigma2, void* x, int x_type, const float* x_scale,
+                      void* workspace, size_t ws_bytes, void* stream);
 /* Uniform start image per frame: c_m = max(sum(s - r), 0) / (kappa dt_m sum(n P 1)),
  * at least 1e-6, written to every voxel of x [Z][ny][nx][M].
  * workspace >= kcs_osl_workspace_size bytes. */
@@ -132,6 +161,11 @@ int kcs_init_image(const kcs_geometry_t* g, int n_frames, const float* frame_dt,
                    const float* counts, const float* randoms, int randoms_layout,
                    const float* bin_factor, float* x, void* workspace, size_t ws_bytes,
                    void* stream);
+/* Precision form: counts as counts_type; x written as x_type holding c_m / x_scale[m]. */
+int kcs_init_image_ex(const kcs_geometry_t* g, int n_frames, const float* frame_dt, float kappa,
+                      const void* counts, int counts_type, const float* randoms,
+                      int randoms_layout, const float* bin_factor, void* x, int x_type,
+                      const float* x_scale, void* workspace, size_t ws_bytes, void* stream);
 
 /* ---------------------------------------------------------- kinetics
  * FDG two-tissue irreversible model with blood fraction (Sec. III-A, IV-A),
@@ -179,6 +213,13 @@ size_t kcs_lm_workspace_size(int nx, int ny, int nz);
 int kcs_map_lm_fit(const kcs_kinetics_t* k, int nx, int ny, int nz, const float* x,
                    float* params, float* lambda, int n_steps, float beta_h, float delta,
                    float* F_out, void* workspace, size_t ws_bytes, void* stream);
+/* Precision form: the image TACs x stored as x_type (KCS_F32/BF16/F16) with
+ * per-frame scale x_scale [M] (NULL = 1); the fit itself is unchanged (float32
+ * model, float64 4x4 solve). */
+int kcs_map_lm_fit_ex(const kcs_kinetics_t* k, int nx, int ny, int nz, const void* x,
+                      int x_type, const float* x_scale, float* params, float* lambda,
+                      int n_steps, float beta_h, float delta, float* F_out, void* workspace,
+                      size_t ws_bytes, void* stream);
 
 /* ------------------------------------------------- MAP-LM without allocation
  * The paper has no counterpart to this entry point; it exists for callers that
@@ -217,11 +258,11 @@ typedef struct kcs_study_desc {
   int n_frames;
   float kappa;             /* count calibration: counts per (activity . mm . min) */
   const float* frame_dt;   /* [M] device                                      */
-  const float* counts;     /* [Z][A][B][M]                                    */
+  const void* counts;      /* [Z][A][B][M], counts_type                       */
   const float* randoms;    /* see randoms_layout                              */
   int randoms_layout;
   const float* bin_factor; /* [Z][A][B] or NULL                               */
-  float* x;                /* [Z][ny][nx][M] in/out                           */
+  void* x;                 /* [Z][ny][nx][M] in/out, x_type                   */
   float* params;           /* [4][Z][ny][nx] in/out                           */
   float* F;                /* [Z][ny][nx][M] out (model TACs of params)       */
   int params_given;        /* nonzero: prior on from the first iteration      */
@@ -230,6 +271,12 @@ typedef struct kcs_study_desc {
   float beta_h, delta;     /* Huber prior (Eq. 4-6)                           */
   void* workspace;         /* >= kcs_study_workspace_size bytes               */
   size_t ws_bytes;
+  /* precision form (zero-initialised = float32 everywhere): counts stored as
+   * counts_type (KCS_F32 / KCS_U16), x and the ratio as x_type (KCS_F32 /
+   * KCS_BF16 / KCS_F16) with per-frame scale x_scale [M] (device, NULL = 1). */
+  int counts_type;
+  int x_type;
+  const float* x_scale;
 } kcs_study_desc_t;
 
 size_t kcs_study_workspace_size(const kcs_geometry_t* g, int n_frames);

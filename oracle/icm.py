@@ -23,10 +23,16 @@ from . import kinetics, lm, osl
 
 def icm(geom, counts, kappa, t_start, t_end, feng, n_iter, n_lm,
         beta_kp, beta_h, delta, x0=None, xi0=None, xi_start=(0.05, 0.10, 0.03, 0.03),
-        bin_factor=None, randoms=None, sigma2=1.0):
+        bin_factor=None, randoms=None, sigma2=1.0, storage=None):
+    """storage = None runs in float64 throughout; storage = "bf16" or "f16"
+    holds the image (and each subset's ratio sinogram) on that grid with the
+    per-frame scale max_v x_vm of the start image (osl.osl_update_stored)."""
     dt = np.asarray(t_end) - np.asarray(t_start)
     Z = counts.shape[0]
     x = osl.initial_image(geom, counts, kappa, dt, Z, bin_factor, randoms) if x0 is None else x0.copy()
+    if storage is not None:
+        scale = x.reshape(-1, x.shape[-1]).max(axis=0)
+        x = osl.quantize(x / scale, storage) * scale
     have_xi = xi0 is not None
     xi = xi0.copy() if have_xi else np.broadcast_to(
         np.asarray(xi_start, float)[:, None, None, None], (4, Z, geom.ny, geom.nx)).copy()
@@ -34,7 +40,16 @@ def icm(geom, counts, kappa, t_start, t_end, feng, n_iter, n_lm,
         F = None
         if n > 0 or have_xi:
             F = kinetics.model_maps(xi, t_start, t_end, feng)
-        x = osl.osl_pass(geom, x, counts, kappa, dt, bin_factor, randoms, F, beta_kp, sigma2)
+        if storage is None:
+            x = osl.osl_pass(geom, x, counts, kappa, dt, bin_factor, randoms, F, beta_kp, sigma2)
+        else:
+            xs = x / scale
+            for k in range(geom.n_subsets):
+                xs = osl.osl_update_stored(
+                    geom, xs, k, osl.subset_slice(counts, geom, k), kappa, dt, scale, storage,
+                    osl.subset_slice(bin_factor, geom, k), osl.subset_slice(randoms, geom, k),
+                    F, beta_kp, sigma2)
+            x = xs * scale
         xi, _ = lm.lm_fit(x, xi, n_lm, t_start, t_end, feng, beta_h, delta)
     F = kinetics.model_maps(xi, t_start, t_end, feng)
     return x, xi, kinetics.ki(xi), F

@@ -20,6 +20,11 @@ towards F; the subset sensitivity replaces the full one and the prior is
 scaled by 1/S so that one pass over the subsets applies beta once; the
 denominator is clamped at 1e-3 of the sensitivity term.
 
+The precision form (image and ratio stored in bfloat16 or float16 with a
+per-frame scale) is the same update with each store rounded to the storage
+grid; quantize() is pinned against IEEE binary16 conversion, against ties and
+exactly representable values of bfloat16, and against its error bound.
+
 Pins (tests/test_oracle_osl.py): with one subset and beta = 0 it is MLEM and
 the Poisson log-likelihood never decreases; x = F makes the prior vanish;
 positivity is preserved; OSEM with S subsets equals S successive MLEM-like
@@ -62,6 +67,45 @@ def osl_update(geom, x, k, counts_k, kappa, dt, bin_factor_k=None, randoms_k=Non
         den = np.maximum(den + g, 1e-3 * den)
     ok = np.broadcast_to(sens[..., None] > 0, x.shape)
     return np.where(ok, x * back / np.where(ok, den, 1.0), x)
+
+
+def quantize(v, kind):
+    """Round float64 values to the storage grid of the precision form, to nearest
+    with ties to even: kind "bf16" keeps 8 significant bits (the float32 exponent
+    range, so every value here is normal), "f16" is IEEE binary16 with values
+    above its largest finite number 65504 saturated; "f32" is IEEE single."""
+    v = np.asarray(v, np.float64)
+    if kind == "f32":
+        return v.astype(np.float32).astype(np.float64)
+    if kind == "f16":
+        return np.minimum(v, 65504.0).astype(np.float16).astype(np.float64)
+    if kind != "bf16":
+        raise ValueError(kind)
+    m, e = np.frexp(v)                       # v = m 2^e, 0.5 <= |m| < 1
+    return np.ldexp(np.round(m * 256.0) / 256.0, e)   # np.round: ties to even
+
+
+def osl_update_stored(geom, xs, k, counts_k, kappa, dt, scale, kind, bin_factor_k=None,
+                      randoms_k=None, F=None, beta=0.0, sigma2=1.0):
+    """The same update in the precision form: the image is held as stored values
+    xs (on the grid of kind) with x = xs * scale[m], the ratio rho is stored on
+    that grid too, and the new image is stored as quantize(x_new / scale).
+    Arithmetic stays in float64 between the stores."""
+    dt = np.asarray(dt, np.float64)
+    scale = np.asarray(scale, np.float64)
+    x = xs * scale
+    ybar = expected_counts(geom, x, k, kappa, dt, bin_factor_k, randoms_k)
+    rho = quantize(np.where(ybar > 0, counts_k / np.where(ybar > 0, ybar, 1.0), 0.0), kind)
+    nd = np.ones(counts_k.shape[:-1]) if bin_factor_k is None else bin_factor_k
+    back = geom.back(rho * nd[..., None], k) * (kappa * dt)
+    sens = geom.back(np.broadcast_to(nd[..., None], nd.shape + (1,)).copy(), k)[..., 0] * kappa
+    den = sens[..., None] * dt
+    if F is not None and beta != 0.0:
+        g = (beta / geom.n_subsets) * (x - F) / sigma2
+        den = np.maximum(den + g, 1e-3 * den)
+    ok = np.broadcast_to(sens[..., None] > 0, x.shape)
+    xn = np.where(ok, x * back / np.where(ok, den, 1.0), x)
+    return quantize(xn / scale, kind)
 
 
 def subset_slice(arr, geom, k):

@@ -41,7 +41,8 @@ class StudyDesc(C.Structure):
                 ("counts", vp), ("randoms", vp), ("randoms_layout", i32), ("bin_factor", vp),
                 ("x", vp), ("params", vp), ("F", vp), ("params_given", i32), ("n_lm", i32),
                 ("beta_kp", f32), ("sigma2", f32), ("beta_h", f32), ("delta", f32),
-                ("workspace", vp), ("ws_bytes", sz)]
+                ("workspace", vp), ("ws_bytes", sz), ("counts_type", i32), ("x_type", i32),
+                ("x_scale", vp)]
 
 
 SIGNATURES = {
@@ -58,6 +59,13 @@ SIGNATURES = {
     "kcs_osl_ratio": (i32, [vp, i32, i32, vp, f32, vp, vp, i32, vp, vp, vp, vp]),
     "kcs_osl_backproject": (i32, [vp, i32, i32, vp, f32, vp, vp, vp, f32, f32, vp, vp]),
     "kcs_init_image": (i32, [vp, i32, vp, f32, vp, vp, i32, vp, vp, vp, sz, vp]),
+    "kcs_osl_ratio_ex": (i32, [vp, i32, i32, vp, f32, vp, i32, vp, i32, vp, vp, i32, vp, vp, vp]),
+    "kcs_osl_backproject_ex": (i32, [vp, i32, i32, vp, f32, vp, vp, vp, f32, f32, vp, i32, vp, vp]),
+    "kcs_osl_update_ex": (i32, [vp, i32, i32, vp, f32, vp, i32, vp, i32, vp, vp, f32, f32, vp, i32,
+                                vp, vp, sz, vp]),
+    "kcs_init_image_ex": (i32, [vp, i32, vp, f32, vp, i32, vp, i32, vp, vp, i32, vp, vp, sz, vp]),
+    "kcs_map_lm_fit_ex": (i32, [vp, i32, i32, i32, vp, i32, vp, vp, vp, i32, f32, f32, vp, vp, sz,
+                                vp]),
     "kcs_create_kinetics": (i32, [pp, i32, dp, dp, dp, vp]),
     "kcs_destroy_kinetics": (i32, [vp]),
     "kcs_tac_eval": (i32, [vp, i64, vp, vp, vp, vp]),

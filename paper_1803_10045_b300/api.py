@@ -15,6 +15,15 @@ import torch
 from ._lib import StudyDesc, check, lib
 
 RANDOMS_NONE, RANDOMS_PER_FRAME, RANDOMS_FULL = 0, 1, 2
+F32, BF16, F16, U16 = 0, 1, 2, 3
+_STORAGE = {torch.float32: F32, torch.bfloat16: BF16, torch.float16: F16, torch.uint16: U16}
+
+
+def _storage(t, allowed, name):
+    code = _STORAGE.get(t.dtype)
+    if code not in allowed:
+        raise ValueError(f"{name} has unsupported dtype {t.dtype}")
+    return code
 
 
 def _stream():
@@ -123,19 +132,23 @@ def osl_workspace_size(g: Geometry, M):
 
 
 def osl_update(g: Geometry, subset, x, frame_dt, kappa, counts, randoms=None, bin_factor=None,
-               F=None, beta=0.0, sigma2=1.0, workspace=None):
-    """One OS-MAP-OSL-KP update of x (in place) on subset k."""
+               F=None, beta=0.0, sigma2=1.0, workspace=None, x_scale=None):
+    """One OS-MAP-OSL-KP update of x (in place) on subset k.  x may be float32,
+    bfloat16 or float16 (stored x / x_scale[m]); counts float32 or uint16."""
     M = x.shape[-1]
     pr, layout = _randoms(g, randoms, M)
+    xt = _storage(x, (F32, BF16, F16), "x")
+    ct = _storage(counts, (F32, U16), "counts")
     if workspace is None:
         workspace = _workspace(osl_workspace_size(g, M), x.device)
-    check(lib.kcs_osl_update(
+    check(lib.kcs_osl_update_ex(
         g.handle, subset, M, _ptr(frame_dt, "frame_dt", (M,)), float(kappa),
-        _ptr(counts, "counts", g.sino_shape(M)), pr, layout,
+        _ptr(counts, "counts", g.sino_shape(M), dtype=counts.dtype), ct, pr, layout,
         _ptr(bin_factor, "bin_factor", (g.nz, g.n_angles, g.n_bins), allow_none=True),
         _ptr(F, "F", g.image_shape(M), allow_none=True), float(beta), float(sigma2),
-        _ptr(x, "x", g.image_shape(M)), C.c_void_p(workspace.data_ptr()), workspace.numel(),
-        _stream()))
+        _ptr(x, "x", g.image_shape(M), dtype=x.dtype), xt,
+        _ptr(x_scale, "x_scale", (M,), allow_none=True), C.c_void_p(workspace.data_ptr()),
+        workspace.numel(), _stream()))
     return x
 
 
@@ -167,20 +180,24 @@ def osl_backproject(g: Geometry, subset, x, frame_dt, kappa, rho, bin_factor=Non
 
 
 def init_image(g: Geometry, frame_dt, kappa, counts, randoms=None, bin_factor=None, out=None,
-               workspace=None):
-    """Uniform per-frame start image matching the measured trues."""
+               workspace=None, dtype=torch.float32, x_scale=None):
+    """Uniform per-frame start image matching the measured trues (stored as
+    dtype holding c_m / x_scale[m])."""
     M = counts.shape[-1]
     pr, layout = _randoms(g, randoms, M)
     if out is None:
-        out = torch.empty(g.image_shape(M), device=counts.device, dtype=torch.float32)
+        out = torch.empty(g.image_shape(M), device=counts.device, dtype=dtype)
+    xt = _storage(out, (F32, BF16, F16), "out")
+    ct = _storage(counts, (F32, U16), "counts")
     if workspace is None:
         workspace = _workspace(osl_workspace_size(g, M), counts.device)
-    check(lib.kcs_init_image(
+    check(lib.kcs_init_image_ex(
         g.handle, M, _ptr(frame_dt, "frame_dt", (M,)), float(kappa),
-        _ptr(counts, "counts", g.sino_shape(M)), pr, layout,
+        _ptr(counts, "counts", g.sino_shape(M), dtype=counts.dtype), ct, pr, layout,
         _ptr(bin_factor, "bin_factor", (g.nz, g.n_angles, g.n_bins), allow_none=True),
-        _ptr(out, "out", g.image_shape(M)), C.c_void_p(workspace.data_ptr()), workspace.numel(),
-        _stream()))
+        _ptr(out, "out", g.image_shape(M), dtype=out.dtype), xt,
+        _ptr(x_scale, "x_scale", (M,), allow_none=True), C.c_void_p(workspace.data_ptr()),
+        workspace.numel(), _stream()))
     return out
 
 
@@ -242,13 +259,16 @@ def lm_workspace_size(nx, ny, nz):
 
 
 def map_lm_fit(kin: Kinetics, x, params, n_steps, beta_h, delta, lam=None, F_out=None,
-               workspace=None):
-    """n_steps MAP-LM steps on params [4][Z][Y][X] (in place) for TACs x [Z][Y][X][M]."""
+               workspace=None, x_scale=None):
+    """n_steps MAP-LM steps on params [4][Z][Y][X] (in place) for TACs x [Z][Y][X][M]
+    (x float32, bfloat16 or float16 holding x / x_scale[m])."""
     nz, ny, nx, M = x.shape
+    xt = _storage(x, (F32, BF16, F16), "x")
     if workspace is None:
         workspace = _workspace(lm_workspace_size(nx, ny, nz), x.device)
-    check(lib.kcs_map_lm_fit(
-        kin.handle, nx, ny, nz, _ptr(x, "x", (nz, ny, nx, M)), _ptr(params, "params", (4, nz, ny, nx)),
+    check(lib.kcs_map_lm_fit_ex(
+        kin.handle, nx, ny, nz, _ptr(x, "x", (nz, ny, nx, M), dtype=x.dtype), xt,
+        _ptr(x_scale, "x_scale", (M,), allow_none=True), _ptr(params, "params", (4, nz, ny, nx)),
         _ptr(lam, "lambda", (nz, ny, nx), allow_none=True), int(n_steps), float(beta_h), float(delta),
         _ptr(F_out, "F_out", (nz, ny, nx, M), allow_none=True), C.c_void_p(workspace.data_ptr()),
         workspace.numel(), _stream()))
@@ -260,7 +280,7 @@ class Study:
 
     def __init__(self, geom: Geometry, kin: Kinetics, frame_dt, kappa, counts, x, params, F=None,
                  randoms=None, bin_factor=None, params_given=False, n_lm=10, beta_kp=0.1,
-                 sigma2=1.0, beta_h=0.1, delta=0.01, workspace=None):
+                 sigma2=1.0, beta_h=0.1, delta=0.01, workspace=None, x_scale=None):
         M = kin.M
         dev = x.device
         if F is None:
@@ -268,16 +288,20 @@ class Study:
         if workspace is None:
             workspace = _workspace(lib.kcs_study_workspace_size(geom.handle, M), dev)
         pr, layout = _randoms(geom, randoms, M)
-        self._keep = (geom, kin, frame_dt, counts, x, params, F, randoms, bin_factor, workspace)
+        self._keep = (geom, kin, frame_dt, counts, x, params, F, randoms, bin_factor, workspace,
+                      x_scale)
         self.geom, self.kin, self.x, self.params, self.F = geom, kin, x, params, F
         d = StudyDesc()
         d.geom, d.kin, d.n_frames, d.kappa = geom.handle, kin.handle, M, float(kappa)
         d.frame_dt = _ptr(frame_dt, "frame_dt", (M,))
-        d.counts = _ptr(counts, "counts", geom.sino_shape(M))
+        d.counts = _ptr(counts, "counts", geom.sino_shape(M), dtype=counts.dtype)
+        d.counts_type = _storage(counts, (F32, U16), "counts")
+        d.x_type = _storage(x, (F32, BF16, F16), "x")
+        d.x_scale = _ptr(x_scale, "x_scale", (M,), allow_none=True)
         d.randoms, d.randoms_layout = pr, layout
         d.bin_factor = _ptr(bin_factor, "bin_factor", (geom.nz, geom.n_angles, geom.n_bins),
                             allow_none=True)
-        d.x = _ptr(x, "x", geom.image_shape(M))
+        d.x = _ptr(x, "x", geom.image_shape(M), dtype=x.dtype)
         d.params = _ptr(params, "params", (4, geom.nz, geom.ny, geom.nx))
         d.F = _ptr(F, "F", geom.image_shape(M))
         d.params_given, d.n_lm = int(bool(params_given)), int(n_lm)

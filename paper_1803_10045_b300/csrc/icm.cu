@@ -29,6 +29,10 @@ int kcs_create_study(kcs_study_t** out, const kcs_study_desc_t* d) {
   KCS_REQUIRE(d->kin->M == d->n_frames, "kinetics has %d frames, study %d", d->kin->M, d->n_frames);
   KCS_REQUIRE(d->frame_dt && d->counts && d->x && d->params && d->F, "NULL device buffer");
   KCS_REQUIRE(d->n_lm >= 0, "n_lm < 0");
+  KCS_REQUIRE(d->x_type == KCS_F32 || d->x_type == KCS_BF16 || d->x_type == KCS_F16,
+              "x_type %d must be KCS_F32, KCS_BF16 or KCS_F16", d->x_type);
+  KCS_REQUIRE(d->counts_type == KCS_F32 || d->counts_type == KCS_U16,
+              "counts_type %d must be KCS_F32 or KCS_U16", d->counts_type);
   KCS_REQUIRE(d->workspace && d->ws_bytes >= kcs_study_workspace_size(d->geom, d->n_frames),
               "workspace too small (%zu < %zu)", d->ws_bytes,
               kcs_study_workspace_size(d->geom, d->n_frames));
@@ -62,14 +66,16 @@ int kcs_icm_iterate(kcs_study_t* st, int n_iter, void* stream) {
       if (rc) return rc;
     }
     for (int k = 0; k < g->S; ++k) {
-      const int rc = kcs_osl_update(g, k, d.n_frames, d.frame_dt, d.kappa, d.counts, d.randoms,
-                                    d.randoms_layout, d.bin_factor, prior ? d.F : nullptr,
-                                    prior ? d.beta_kp : 0.f, d.sigma2 > 0.f ? d.sigma2 : 1.f, d.x,
-                                    d.workspace, d.ws_bytes, stream);
+      const int rc = kcs_osl_update_ex(g, k, d.n_frames, d.frame_dt, d.kappa, d.counts,
+                                       d.counts_type, d.randoms, d.randoms_layout, d.bin_factor,
+                                       prior ? d.F : nullptr, prior ? d.beta_kp : 0.f,
+                                       d.sigma2 > 0.f ? d.sigma2 : 1.f, d.x, d.x_type, d.x_scale,
+                                       d.workspace, d.ws_bytes, stream);
       if (rc) return rc;
     }
-    const int rc = kcs_map_lm_fit(d.kin, g->nx, g->ny, g->nz, d.x, d.params, nullptr, d.n_lm,
-                                  d.beta_h, d.delta, d.F, d.workspace, d.ws_bytes, stream);
+    const int rc = kcs_map_lm_fit_ex(d.kin, g->nx, g->ny, g->nz, d.x, d.x_type, d.x_scale,
+                                     d.params, nullptr, d.n_lm, d.beta_h, d.delta, d.F,
+                                     d.workspace, d.ws_bytes, stream);
     if (rc) return rc;
     st->iterations += 1;
   }

@@ -444,7 +444,8 @@ constexpr float TAU = 1e-5f;
 struct LmArgs {
   KinDev kd;
   int nx, ny, nz;
-  const float* x;        // [V][M]
+  const void* x;         // [V][M], storage type of the kernel instance
+  const float* x_scale;  // [M] per-frame scale of a stored image (null: 1)
   const float* p_in;     // [4][V]
   float* p_out;          // [4][V]
   float* lambda;         // [V]
@@ -554,6 +555,7 @@ __device__ __forceinline__ void huber_terms(const LmArgs& L, long long V, long l
     }
 }
 
+template <class TX>
 __global__ void __launch_bounds__(LM_THREADS, KCS_LM_MINBLOCKS) k_lm_step(LmArgs L) {
   extern __shared__ float xs_all[];
   const int M = L.kd.M;
@@ -562,9 +564,11 @@ __global__ void __launch_bounds__(LM_THREADS, KCS_LM_MINBLOCKS) k_lm_step(LmArgs
   const long long V = (long long)L.nx * L.ny * L.nz;
   const long long v0 = (long long)blockIdx.x * LM_BLOCK_VOX;
   const long long nv = min((long long)LM_BLOCK_VOX, V - v0);
+  const TX* xg = static_cast<const TX*>(L.x);
   for (long long e = threadIdx.x; e < nv * M; e += LM_THREADS) {
     const long long r = e / M, m = e - r * M;
-    xs_all[r * ld + m] = L.x[v0 * M + e];
+    const float xv = ld1(xg + v0 * M + e);
+    xs_all[r * ld + m] = L.x_scale ? xv * __ldg(L.x_scale + m) : xv;
   }
   __syncthreads();
   long long vv[LM_VPT];
@@ -817,12 +821,15 @@ size_t kcs_lm_workspace_size(int nx, int ny, int nz) {
   return align256(4 * V * sizeof(float)) + align256(V * sizeof(float));
 }
 
-int kcs_map_lm_fit(const kcs_kinetics_t* k, int nx, int ny, int nz, const float* x, float* params,
-                   float* lambda, int n_steps, float beta_h, float delta, float* F_out,
-                   void* workspace, size_t ws_bytes, void* stream) {
+int kcs_map_lm_fit_ex(const kcs_kinetics_t* k, int nx, int ny, int nz, const void* x,
+                      int x_type, const float* x_scale, float* params, float* lambda,
+                      int n_steps, float beta_h, float delta, float* F_out, void* workspace,
+                      size_t ws_bytes, void* stream) {
   clear_error();
   KCS_REQUIRE(k && x && params, "NULL argument");
   KCS_REQUIRE(nx > 0 && ny > 0 && nz > 0, "sizes must be positive");
+  KCS_REQUIRE(x_type == KCS_F32 || x_type == KCS_BF16 || x_type == KCS_F16,
+              "x_type %d must be KCS_F32, KCS_BF16 or KCS_F16", x_type);
   KCS_REQUIRE(n_steps >= 0, "n_steps < 0");
   KCS_REQUIRE(delta > 0.f && beta_h >= 0.f, "need delta > 0 and beta_h >= 0");
   KCS_REQUIRE(workspace && ws_bytes >= kcs_lm_workspace_size(nx, ny, nz),
@@ -836,11 +843,14 @@ int kcs_map_lm_fit(const kcs_kinetics_t* k, int nx, int ny, int nz, const float*
   L.kd = k->dev();
   L.nx = nx; L.ny = ny; L.nz = nz;
   L.x = x;
+  L.x_scale = x_scale;
   L.lambda = lambda ? lambda : lam_ws;
   L.beta = beta_h;
   L.delta = delta;
   const size_t smem = sizeof(float) * LM_BLOCK_VOX * (k->M + 1) * 2;
-  KCS_CUDA(cudaFuncSetAttribute(k_lm_step, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  auto kern = x_type == KCS_BF16 ? k_lm_step<__nv_bfloat16>
+            : x_type == KCS_F16 ? k_lm_step<__half> : k_lm_step<float>;
+  KCS_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   const unsigned blocks = (unsigned)((V + LM_BLOCK_VOX - 1) / LM_BLOCK_VOX);
   float* cur = params;
   float* nxt = pong;
@@ -848,7 +858,7 @@ int kcs_map_lm_fit(const kcs_kinetics_t* k, int nx, int ny, int nz, const float*
     L.p_in = cur;
     L.p_out = nxt;
     L.reset_lambda = (it == 0 && !lambda) ? 1 : 0;
-    k_lm_step<<<blocks, LM_THREADS, smem, s>>>(L);
+    kern<<<blocks, LM_THREADS, smem, s>>>(L);
     KCS_LAUNCHED();
     std::swap(cur, nxt);
   }
@@ -856,6 +866,13 @@ int kcs_map_lm_fit(const kcs_kinetics_t* k, int nx, int ny, int nz, const float*
     KCS_CUDA(cudaMemcpyAsync(params, cur, 4 * (size_t)V * sizeof(float), cudaMemcpyDeviceToDevice, s));
   if (F_out) return launch_tac_eval(k, V, params, F_out, nullptr, s);
   return KCS_OK;
+}
+
+int kcs_map_lm_fit(const kcs_kinetics_t* k, int nx, int ny, int nz, const float* x, float* params,
+                   float* lambda, int n_steps, float beta_h, float delta, float* F_out,
+                   void* workspace, size_t ws_bytes, void* stream) {
+  return kcs_map_lm_fit_ex(k, nx, ny, nz, x, KCS_F32, nullptr, params, lambda, n_steps, beta_h,
+                           delta, F_out, workspace, ws_bytes, stream);
 }
 
 }  // extern "C"

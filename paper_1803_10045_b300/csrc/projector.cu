@@ -39,6 +39,60 @@ __device__ __forceinline__ void fma4(float4& acc, float s, const float4& v) {
   acc.w = fmaf(s, v.w, acc.w);
 }
 
+// 4 consecutive stored values <-> float4 (storage types of the precision form:
+// float, bfloat16, half; uint16 counts).  Conversions round to nearest.
+__device__ __forceinline__ float4 load4(const float* p) { return __ldg(reinterpret_cast<const float4*>(p)); }
+__device__ __forceinline__ float4 load4(const __nv_bfloat16* p) {
+  const uint2 u = __ldg(reinterpret_cast<const uint2*>(p));
+  const float2 a = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&u.x));
+  const float2 b = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&u.y));
+  return make_float4(a.x, a.y, b.x, b.y);
+}
+__device__ __forceinline__ float4 load4(const __half* p) {
+  const uint2 u = __ldg(reinterpret_cast<const uint2*>(p));
+  const float2 a = __half22float2(*reinterpret_cast<const __half2*>(&u.x));
+  const float2 b = __half22float2(*reinterpret_cast<const __half2*>(&u.y));
+  return make_float4(a.x, a.y, b.x, b.y);
+}
+__device__ __forceinline__ float4 load4(const uint16_t* p) {
+  const uint2 u = __ldg(reinterpret_cast<const uint2*>(p));
+  return make_float4((float)(u.x & 0xffffu), (float)(u.x >> 16), (float)(u.y & 0xffffu),
+                     (float)(u.y >> 16));
+}
+// plain (non-__ldg) loads for in-place read-modify-write of the image
+__device__ __forceinline__ float4 ld4(const float* p) { return *reinterpret_cast<const float4*>(p); }
+__device__ __forceinline__ float4 ld4(const __nv_bfloat16* p) {
+  const uint2 u = *reinterpret_cast<const uint2*>(p);
+  const float2 a = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&u.x));
+  const float2 b = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&u.y));
+  return make_float4(a.x, a.y, b.x, b.y);
+}
+__device__ __forceinline__ float4 ld4(const __half* p) {
+  const uint2 u = *reinterpret_cast<const uint2*>(p);
+  const float2 a = __half22float2(*reinterpret_cast<const __half2*>(&u.x));
+  const float2 b = __half22float2(*reinterpret_cast<const __half2*>(&u.y));
+  return make_float4(a.x, a.y, b.x, b.y);
+}
+__device__ __forceinline__ void st4(float* p, float4 v) { *reinterpret_cast<float4*>(p) = v; }
+__device__ __forceinline__ void st4(__nv_bfloat16* p, float4 v) {
+  uint2 u;
+  *reinterpret_cast<__nv_bfloat162*>(&u.x) = __float22bfloat162_rn(make_float2(v.x, v.y));
+  *reinterpret_cast<__nv_bfloat162*>(&u.y) = __float22bfloat162_rn(make_float2(v.z, v.w));
+  *reinterpret_cast<uint2*>(p) = u;
+}
+__device__ __forceinline__ void st4(__half* p, float4 v) {
+  // saturate to the largest finite half instead of overflowing to infinity
+  const float mx = 65504.f;
+  v = make_float4(fminf(v.x, mx), fminf(v.y, mx), fminf(v.z, mx), fminf(v.w, mx));
+  uint2 u;
+  *reinterpret_cast<__half2*>(&u.x) = __float22half2_rn(make_float2(v.x, v.y));
+  *reinterpret_cast<__half2*>(&u.y) = __float22half2_rn(make_float2(v.z, v.w));
+  *reinterpret_cast<uint2*>(p) = u;
+}
+__device__ __forceinline__ float4 mul4(float4 a, float4 b) {
+  return make_float4(a.x * b.x, a.y * b.y, a.z * b.z, a.w * b.w);
+}
+
 // Fractional minor index of centred bin bf given inner = fma(tf, gamma, centre)
 // (shared by both kernels, explicit fused multiply-adds: identical bits).
 __device__ __forceinline__ float minor_pos(float bf, float beta, float inner) {
@@ -49,16 +103,17 @@ __device__ __forceinline__ float inner_pos(float tf, float gamma, float centre) 
 }
 
 struct ProjArgs {
-  const float4* x;        // image (forward input / OSL in-out)
-  float4* xout;           // image output (back-projection)
-  const float4* y;        // subset sinogram input (back-projection)
-  float4* yout;           // subset sinogram output (forward)
+  const void* x;          // image (forward input / OSL in-out), storage type TX
+  void* xout;             // image output (back-projection)
+  const void* y;          // subset sinogram input (back-projection), storage type TY
+  void* yout;             // subset sinogram output (forward)
+  const float4* xscale;   // per-frame scale of a stored image [MQ] (null: 1)
   const AngleTab* ang;
   const int* sub;         // angle indices of the subset
   int n_sub;
   int nx, ny, nz, B, A;
   // ratio / OSL terms
-  const float4* counts;   // [Z][A][B][MQ]
+  const void* counts;     // [Z][A][B][M], storage type TC
   const float4* randoms;  // per frame [MQ] or full [Z][A][B][MQ]
   int randoms_layout;
   const float* bin_factor;  // [Z][A][B] or null
@@ -70,7 +125,7 @@ struct ProjArgs {
 
 // Forward projection of every frame of rays (z, ak, b); RATIO replaces the
 // projection by rho = s / (kappa dt n_d (P x) + r).
-template <int MQ, bool RATIO>
+template <int MQ, bool RATIO, class TX, class TC, class TY>
 __global__ void __launch_bounds__(256) k_forward(ProjArgs p) {
   constexpr int RPW = 32 / MQ;
   const int lane = threadIdx.x & 31;
@@ -88,12 +143,12 @@ __global__ void __launch_bounds__(256) k_forward(ProjArgs p) {
   const AngleTab T = p.ang[a];
   const int n_major = T.xmajor ? p.nx : p.ny;
   const int n_minor = T.xmajor ? p.ny : p.nx;
-  const int s_major = T.xmajor ? MQ : p.nx * MQ;   // float4 stride of one major step
-  const int s_minor = T.xmajor ? p.nx * MQ : MQ;   // float4 stride of one minor step
+  const int s_major = T.xmajor ? 4 * MQ : p.nx * 4 * MQ;   // element stride of a major step
+  const int s_minor = T.xmajor ? p.nx * 4 * MQ : 4 * MQ;   // element stride of a minor step
   const float tc = 0.5f * (float)(n_major - 1);
   const float centre = 0.5f * (float)(n_minor - 1);
   const float bf = (float)b - 0.5f * (float)(p.B - 1);
-  const float4* xz = p.x + (size_t)z * p.ny * p.nx * MQ + q;
+  const TX* xz = static_cast<const TX*>(p.x) + ((size_t)z * p.ny * p.nx * MQ + q) * 4;
 
   // Conservative major-step range where the ray can touch the grid; the exact
   // test is repeated per step below.
@@ -123,9 +178,9 @@ __global__ void __launch_bounds__(256) k_forward(ProjArgs p) {
       const float f = fr - fl;
       const bool in0 = t <= t1 && j0 >= 0 && j0 < n_minor;
       const bool in1 = t <= t1 && j0 >= -1 && j0 + 1 < n_minor;
-      const float4* px = xz + (ptrdiff_t)t * s_major + (ptrdiff_t)j0 * s_minor;
-      v0[u] = in0 ? __ldg(px) : f4(0.f);
-      v1[u] = in1 ? __ldg(px + s_minor) : f4(0.f);
+      const TX* px = xz + (ptrdiff_t)t * s_major + (ptrdiff_t)j0 * s_minor;
+      v0[u] = in0 ? load4(px) : f4(0.f);
+      v1[u] = in1 ? load4(px + s_minor) : f4(0.f);
       w0[u] = in0 ? 1.0f - f : 0.f;
       w1[u] = in1 ? f : 0.f;
     }
@@ -136,15 +191,16 @@ __global__ void __launch_bounds__(256) k_forward(ProjArgs p) {
     }
   }
   acc.x *= T.w; acc.y *= T.w; acc.z *= T.w; acc.w *= T.w;
+  if (p.xscale) acc = mul4(acc, __ldg(p.xscale + q));     // stored image -> activity
   const size_t oi = ((size_t)(z * p.n_sub + ak) * p.B + b) * MQ + q;
   if (!RATIO) {
-    p.yout[oi] = acc;
+    st4(static_cast<TY*>(p.yout) + oi * 4, acc);
     return;
   }
   const size_t bin = (size_t)(z * p.A + a) * p.B + b;
   const float nd = p.bin_factor ? __ldg(p.bin_factor + bin) : 1.0f;
   const float4 dt = __ldg(p.dt + q);
-  const float4 s = __ldg(p.counts + bin * MQ + q);
+  const float4 s = load4(static_cast<const TC*>(p.counts) + (bin * MQ + q) * 4);
   float4 r = f4(0.f);
   if (p.randoms_layout == KCS_RANDOMS_PER_FRAME) r = __ldg(p.randoms + q);
   else if (p.randoms_layout == KCS_RANDOMS_FULL) r = __ldg(p.randoms + bin * MQ + q);
@@ -158,7 +214,7 @@ __global__ void __launch_bounds__(256) k_forward(ProjArgs p) {
   rho.y = yb.y > 0.f ? s.y / yb.y : 0.f;
   rho.z = yb.z > 0.f ? s.z / yb.z : 0.f;
   rho.w = yb.w > 0.f ? s.w / yb.w : 0.f;
-  p.yout[oi] = rho;
+  st4(static_cast<TY*>(p.yout) + oi * 4, rho);
 }
 
 // Bins whose sample at this major step can land in [m-1, m+1): the real-valued
@@ -198,7 +254,7 @@ constexpr int BK_ACHUNK = 12;
 
 __host__ __device__ constexpr int bk_pitch(int MQ) { return MQ | 1; }
 
-template <int MQ, int MODE>
+template <int MQ, int MODE, class TX, class TY>
 __global__ void __launch_bounds__(BK_TILE * BK_TILE) k_back_tiled(ProjArgs p, int rows_max,
                                                                    int achunk) {
   constexpr int PITCH = bk_pitch(MQ);
@@ -251,12 +307,13 @@ __global__ void __launch_bounds__(BK_TILE * BK_TILE) k_back_tiled(ProjArgs p, in
     }
     __syncthreads();
     for (int c = 0; c < na; ++c) {
-      const float4* src = p.y + ((size_t)(z * p.n_sub + a0 + c) * p.B + s_lo[c]) * MQ;
+      const TY* src = static_cast<const TY*>(p.y) +
+                      ((size_t)(z * p.n_sub + a0 + c) * p.B + s_lo[c]) * MQ * 4;
       float4* dst = srho + (size_t)c * rows_max * PITCH;
       const int n = s_cnt[c] * MQ;
       for (int e = threadIdx.x; e < n; e += BK_TILE * BK_TILE) {
         const int r = e / MQ, q = e - r * MQ;
-        dst[r * PITCH + q] = __ldg(src + e);
+        dst[r * PITCH + q] = load4(src + (size_t)e * 4);
       }
     }
     __syncthreads();
@@ -300,14 +357,16 @@ __global__ void __launch_bounds__(BK_TILE * BK_TILE) k_back_tiled(ProjArgs p, in
   const size_t vi = ((size_t)(z * p.ny + j) * p.nx + i) * MQ;
   if (MODE == 0) {
 #pragma unroll
-    for (int q = 0; q < MQ; ++q) p.xout[vi + q] = acc[q];
+    for (int q = 0; q < MQ; ++q) st4(static_cast<TX*>(p.xout) + (vi + q) * 4, acc[q]);
     return;
   }
   if (!(sens > 0.f)) return;   // x unchanged where no ray of the subset sees the voxel
   const float ks = p.kappa * sens;
 #pragma unroll
   for (int q = 0; q < MQ; ++q) {
-    float4 xv = p.x[vi + q];
+    float4 xv = ld4(static_cast<const TX*>(p.x) + (vi + q) * 4);
+    const float4 sc = p.xscale ? __ldg(p.xscale + q) : f4(1.f);
+    if (p.xscale) xv = mul4(xv, sc);            // stored image -> activity
     const float4 dt = __ldg(p.dt + q);
     float4 den = make_float4(dt.x * ks, dt.y * ks, dt.z * ks, dt.w * ks);
     if (p.F) {
@@ -322,7 +381,8 @@ __global__ void __launch_bounds__(BK_TILE * BK_TILE) k_back_tiled(ProjArgs p, in
     xv.y = xv.y * (p.kappa * dt.y * acc[q].y) / den.y;
     xv.z = xv.z * (p.kappa * dt.z * acc[q].z) / den.z;
     xv.w = xv.w * (p.kappa * dt.w * acc[q].w) / den.w;
-    p.xout[vi + q] = xv;
+    if (p.xscale) xv = make_float4(xv.x / sc.x, xv.y / sc.y, xv.z / sc.z, xv.w / sc.w);
+    st4(static_cast<TX*>(p.xout) + (vi + q) * 4, xv);
   }
 }
 
@@ -370,7 +430,9 @@ __global__ void __launch_bounds__(256) k_sens(ProjArgs p, float* sens_out) {
 // counts - randoms, and the total of n_d (P 1)_d = sum_v sens_v.
 constexpr int RED_BLOCKS = 512;
 
-__global__ void __launch_bounds__(256) k_partial_sums(const float* data, long long n_rows, int M,
+
+template <class T>
+__global__ void __launch_bounds__(256) k_partial_sums(const T* data, long long n_rows, int M,
                                                       double* partial /*[RED_BLOCKS][M]*/) {
   __shared__ double sh[256];
   const int tid = threadIdx.x;
@@ -379,7 +441,7 @@ __global__ void __launch_bounds__(256) k_partial_sums(const float* data, long lo
   const long long r1 = min(n_rows, r0 + per);
   for (int m = 0; m < M; ++m) {
     double s = 0.0;
-    for (long long r = r0 + tid; r < r1; r += blockDim.x) s += (double)data[r * M + m];
+    for (long long r = r0 + tid; r < r1; r += blockDim.x) s += (double)ld1(data + r * M + m);
     sh[tid] = s;
     __syncthreads();
     for (int w = blockDim.x / 2; w > 0; w >>= 1) {
@@ -407,10 +469,13 @@ __global__ void k_init_fill(const double* pc, const double* pr, const double* ps
   cval[m] = (float)fmax(c, 1e-6);
 }
 
-__global__ void k_broadcast_frames(float* x, long long n_vox, int M, const float* cval) {
+template <class TX>
+__global__ void k_broadcast_frames(TX* x, long long n_vox, int M, const float* cval,
+                                   const float* scale) {
   const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (idx >= n_vox * M) return;
-  x[idx] = cval[idx % M];
+  const int m = (int)(idx % M);
+  st1(x + idx, scale ? cval[m] / scale[m] : cval[m]);
 }
 
 // ------------------------------------------------------------ launch helpers
@@ -433,22 +498,40 @@ static ProjArgs base_args(const kcs_geometry* g, int subset) {
   return p;
 }
 
-template <bool RATIO>
-static void launch_forward(int MQ, const ProjArgs& p, cudaStream_t s) {
+template <bool RATIO, class TX, class TC, class TY>
+static void launch_forward_t(int MQ, const ProjArgs& p, cudaStream_t s) {
   const int rpw = 32 / MQ;
   const long long rays = (long long)p.nz * p.n_sub * p.B;
   const long long warps = (rays + rpw - 1) / rpw;
   const unsigned blocks = (unsigned)((warps + 7) / 8);
   switch (MQ) {
-    case 1: k_forward<1, RATIO><<<blocks, 256, 0, s>>>(p); break;
-    case 2: k_forward<2, RATIO><<<blocks, 256, 0, s>>>(p); break;
-    case 3: k_forward<3, RATIO><<<blocks, 256, 0, s>>>(p); break;
-    case 4: k_forward<4, RATIO><<<blocks, 256, 0, s>>>(p); break;
-    case 5: k_forward<5, RATIO><<<blocks, 256, 0, s>>>(p); break;
-    case 6: k_forward<6, RATIO><<<blocks, 256, 0, s>>>(p); break;
-    case 7: k_forward<7, RATIO><<<blocks, 256, 0, s>>>(p); break;
-    case 8: k_forward<8, RATIO><<<blocks, 256, 0, s>>>(p); break;
+    case 1: k_forward<1, RATIO, TX, TC, TY><<<blocks, 256, 0, s>>>(p); break;
+    case 2: k_forward<2, RATIO, TX, TC, TY><<<blocks, 256, 0, s>>>(p); break;
+    case 3: k_forward<3, RATIO, TX, TC, TY><<<blocks, 256, 0, s>>>(p); break;
+    case 4: k_forward<4, RATIO, TX, TC, TY><<<blocks, 256, 0, s>>>(p); break;
+    case 5: k_forward<5, RATIO, TX, TC, TY><<<blocks, 256, 0, s>>>(p); break;
+    case 6: k_forward<6, RATIO, TX, TC, TY><<<blocks, 256, 0, s>>>(p); break;
+    case 7: k_forward<7, RATIO, TX, TC, TY><<<blocks, 256, 0, s>>>(p); break;
+    case 8: k_forward<8, RATIO, TX, TC, TY><<<blocks, 256, 0, s>>>(p); break;
   }
+}
+
+// Plain forward projection (float image -> float sinogram).
+static void launch_forward(int MQ, const ProjArgs& p, cudaStream_t s) {
+  launch_forward_t<false, float, float, float>(MQ, p, s);
+}
+
+// Forward + ratio with a stored image of type tx (the ratio is stored the same
+// way) and counts of type tc.
+template <class TX>
+static void launch_ratio_tx(int MQ, int tc, const ProjArgs& p, cudaStream_t s) {
+  if (tc == KCS_U16) launch_forward_t<true, TX, uint16_t, TX>(MQ, p, s);
+  else launch_forward_t<true, TX, float, TX>(MQ, p, s);
+}
+static void launch_ratio(int MQ, int tx, int tc, const ProjArgs& p, cudaStream_t s) {
+  if (tx == KCS_BF16) launch_ratio_tx<__nv_bfloat16>(MQ, tc, p, s);
+  else if (tx == KCS_F16) launch_ratio_tx<__half>(MQ, tc, p, s);
+  else launch_ratio_tx<float>(MQ, tc, p, s);
 }
 
 // Rows of one angle a 16 x 16 tile can touch: the candidate span over the tile
@@ -461,33 +544,44 @@ static int back_rows_max(const kcs_geometry* g) {
 
 constexpr size_t BK_SMEM_MAX = 200 * 1024;   // dynamic shared memory budget per block
 
-template <int MQ, int MODE>
+template <int MQ, int MODE, class TX, class TY>
 static int launch_back_mq(const ProjArgs& p, int rows_max, cudaStream_t s) {
   const size_t row_bytes = sizeof(float4) * rows_max * bk_pitch(MQ);
   const int achunk = (int)std::min<size_t>(BK_ACHUNK, BK_SMEM_MAX / row_bytes);
   KCS_REQUIRE(achunk >= 1, "bins are too fine relative to voxels for the tiled back-projection");
   const size_t smem = row_bytes * achunk;
-  KCS_CUDA(cudaFuncSetAttribute(k_back_tiled<MQ, MODE>,
+  KCS_CUDA(cudaFuncSetAttribute(k_back_tiled<MQ, MODE, TX, TY>,
                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   const long long tiles = (long long)((p.nx + BK_TILE - 1) / BK_TILE) *
                           ((p.ny + BK_TILE - 1) / BK_TILE) * p.nz;
-  k_back_tiled<MQ, MODE><<<(unsigned)tiles, BK_TILE * BK_TILE, smem, s>>>(p, rows_max, achunk);
+  k_back_tiled<MQ, MODE, TX, TY><<<(unsigned)tiles, BK_TILE * BK_TILE, smem, s>>>(p, rows_max,
+                                                                                achunk);
   return KCS_OK;
 }
 
-template <int MODE>
-static int launch_back(int MQ, const ProjArgs& p, int rows_max, cudaStream_t s) {
+template <int MODE, class TX, class TY>
+static int launch_back_t(int MQ, const ProjArgs& p, int rows_max, cudaStream_t s) {
   switch (MQ) {
-    case 1: return launch_back_mq<1, MODE>(p, rows_max, s);
-    case 2: return launch_back_mq<2, MODE>(p, rows_max, s);
-    case 3: return launch_back_mq<3, MODE>(p, rows_max, s);
-    case 4: return launch_back_mq<4, MODE>(p, rows_max, s);
-    case 5: return launch_back_mq<5, MODE>(p, rows_max, s);
-    case 6: return launch_back_mq<6, MODE>(p, rows_max, s);
-    case 7: return launch_back_mq<7, MODE>(p, rows_max, s);
-    case 8: return launch_back_mq<8, MODE>(p, rows_max, s);
+    case 1: return launch_back_mq<1, MODE, TX, TY>(p, rows_max, s);
+    case 2: return launch_back_mq<2, MODE, TX, TY>(p, rows_max, s);
+    case 3: return launch_back_mq<3, MODE, TX, TY>(p, rows_max, s);
+    case 4: return launch_back_mq<4, MODE, TX, TY>(p, rows_max, s);
+    case 5: return launch_back_mq<5, MODE, TX, TY>(p, rows_max, s);
+    case 6: return launch_back_mq<6, MODE, TX, TY>(p, rows_max, s);
+    case 7: return launch_back_mq<7, MODE, TX, TY>(p, rows_max, s);
+    case 8: return launch_back_mq<8, MODE, TX, TY>(p, rows_max, s);
   }
   return KCS_ERR_INVALID_ARG;
+}
+
+// MODE 0: float sinogram -> float image.  MODE 1: OSL update of an image stored
+// as tx from a ratio stored the same way.
+template <int MODE>
+static int launch_back(int MQ, int tx, const ProjArgs& p, int rows_max, cudaStream_t s) {
+  if (MODE == 0) return launch_back_t<0, float, float>(MQ, p, rows_max, s);
+  if (tx == KCS_BF16) return launch_back_t<MODE, __nv_bfloat16, __nv_bfloat16>(MQ, p, rows_max, s);
+  if (tx == KCS_F16) return launch_back_t<MODE, __half, __half>(MQ, p, rows_max, s);
+  return launch_back_t<MODE, float, float>(MQ, p, rows_max, s);
 }
 
 }  // namespace kcs
@@ -497,7 +591,7 @@ using namespace kcs;
 extern "C" {
 
 const char* kcs_last_error(void) { return kcs::g_err.c_str(); }
-int kcs_version(void) { return 1; }
+int kcs_version(void) { return 2; }
 
 int kcs_create_geometry(kcs_geometry_t** out, int nx, int ny, int nz, float vox_mm, int n_bins,
                         int n_angles, float bin_mm, int n_subsets) {
@@ -593,9 +687,9 @@ int kcs_forward_project(const kcs_geometry_t* g, int subset, int n_frames, const
   KCS_REQUIRE(x && y, "x and y must be device pointers");
   KCS_REQUIRE(aligned16(x) && aligned16(y), "arrays must be 16-byte aligned");
   ProjArgs p = base_args(g, subset);
-  p.x = reinterpret_cast<const float4*>(x);
-  p.yout = reinterpret_cast<float4*>(y);
-  launch_forward<false>(n_frames / 4, p, as_stream(stream));
+  p.x = x;
+  p.yout = y;
+  launch_forward(n_frames / 4, p, as_stream(stream));
   KCS_LAUNCHED();
   return KCS_OK;
 }
@@ -608,9 +702,9 @@ int kcs_back_project(const kcs_geometry_t* g, int subset, int n_frames, const fl
   KCS_REQUIRE(x && y, "x and y must be device pointers");
   KCS_REQUIRE(aligned16(x) && aligned16(y), "arrays must be 16-byte aligned");
   ProjArgs p = base_args(g, subset);
-  p.y = reinterpret_cast<const float4*>(y);
-  p.xout = reinterpret_cast<float4*>(x);
-  st = launch_back<0>(n_frames / 4, p, back_rows_max(g), as_stream(stream));
+  p.y = y;
+  p.xout = x;
+  st = launch_back<0>(n_frames / 4, KCS_F32, p, back_rows_max(g), as_stream(stream));
   if (st) return st;
   KCS_LAUNCHED();
   return KCS_OK;
@@ -639,30 +733,78 @@ size_t kcs_osl_workspace_size(const kcs_geometry_t* g, int n_frames) {
   return align256(std::max(rho, red));
 }
 
-int kcs_osl_ratio(const kcs_geometry_t* g, int subset, int n_frames, const float* frame_dt,
-                  float kappa, const float* counts, const float* randoms, int randoms_layout,
-                  const float* bin_factor, const float* x, float* rho, void* stream) {
+static bool storage_ok(int t) { return t == KCS_F32 || t == KCS_BF16 || t == KCS_F16; }
+static bool aligned_for(const void* ptr, int t) {
+  return ((uintptr_t)ptr & (t == KCS_F32 ? 15u : 7u)) == 0;
+}
+
+int kcs_osl_ratio_ex(const kcs_geometry_t* g, int subset, int n_frames, const float* frame_dt,
+                     float kappa, const void* counts, int counts_type, const float* randoms,
+                     int randoms_layout, const float* bin_factor, const void* x, int x_type,
+                     const float* x_scale, void* rho, void* stream) {
   clear_error();
   int st = check_geom(g, subset, n_frames);
   if (st) return st;
   KCS_REQUIRE(subset >= 0, "the ratio needs a subset index >= 0");
   KCS_REQUIRE(frame_dt && counts && x && rho, "frame_dt, counts, x and rho must be device pointers");
+  KCS_REQUIRE(storage_ok(x_type), "x_type %d must be KCS_F32, KCS_BF16 or KCS_F16", x_type);
+  KCS_REQUIRE(counts_type == KCS_F32 || counts_type == KCS_U16, "counts_type %d must be KCS_F32 or KCS_U16",
+              counts_type);
   KCS_REQUIRE(randoms_layout >= KCS_RANDOMS_NONE && randoms_layout <= KCS_RANDOMS_FULL,
               "bad randoms_layout %d", randoms_layout);
   KCS_REQUIRE(randoms_layout == KCS_RANDOMS_NONE || randoms, "randoms pointer is NULL");
   KCS_REQUIRE(kappa > 0.f, "kappa must be positive");
-  KCS_REQUIRE(aligned16(x) && aligned16(counts) && aligned16(frame_dt) && aligned16(rho) &&
-              aligned16(randoms), "arrays must be 16-byte aligned");
+  KCS_REQUIRE(aligned_for(x, x_type) && aligned_for(rho, x_type) &&
+              aligned_for(counts, counts_type == KCS_U16 ? KCS_BF16 : KCS_F32) && aligned16(frame_dt) &&
+              aligned16(randoms) && aligned16(x_scale), "arrays misaligned (16 B for float, 8 B for 16-bit)");
   ProjArgs p = base_args(g, subset);
-  p.x = reinterpret_cast<const float4*>(x);
-  p.yout = reinterpret_cast<float4*>(rho);
-  p.counts = reinterpret_cast<const float4*>(counts);
+  p.x = x;
+  p.xscale = reinterpret_cast<const float4*>(x_scale);
+  p.yout = rho;
+  p.counts = counts;
   p.randoms = reinterpret_cast<const float4*>(randoms);
   p.randoms_layout = randoms_layout;
   p.bin_factor = bin_factor;
   p.dt = reinterpret_cast<const float4*>(frame_dt);
   p.kappa = kappa;
-  launch_forward<true>(n_frames / 4, p, as_stream(stream));
+  launch_ratio(n_frames / 4, x_type, counts_type, p, as_stream(stream));
+  KCS_LAUNCHED();
+  return KCS_OK;
+}
+
+int kcs_osl_ratio(const kcs_geometry_t* g, int subset, int n_frames, const float* frame_dt,
+                  float kappa, const float* counts, const float* randoms, int randoms_layout,
+                  const float* bin_factor, const float* x, float* rho, void* stream) {
+  return kcs_osl_ratio_ex(g, subset, n_frames, frame_dt, kappa, counts, KCS_F32, randoms,
+                          randoms_layout, bin_factor, x, KCS_F32, nullptr, rho, stream);
+}
+
+int kcs_osl_backproject_ex(const kcs_geometry_t* g, int subset, int n_frames,
+                           const float* frame_dt, float kappa, const float* bin_factor,
+                           const void* rho, const float* F_model, float beta_kp, float sigma2,
+                           void* x, int x_type, const float* x_scale, void* stream) {
+  clear_error();
+  int st = check_geom(g, subset, n_frames);
+  if (st) return st;
+  KCS_REQUIRE(subset >= 0, "the OSL update needs a subset index >= 0");
+  KCS_REQUIRE(frame_dt && rho && x, "frame_dt, rho and x must be device pointers");
+  KCS_REQUIRE(storage_ok(x_type), "x_type %d must be KCS_F32, KCS_BF16 or KCS_F16", x_type);
+  KCS_REQUIRE(kappa > 0.f, "kappa must be positive");
+  KCS_REQUIRE(!F_model || beta_kp == 0.f || sigma2 > 0.f, "sigma2 must be positive");
+  KCS_REQUIRE(aligned_for(x, x_type) && aligned_for(rho, x_type) && aligned16(frame_dt) &&
+              aligned16(F_model) && aligned16(x_scale), "arrays misaligned");
+  ProjArgs q = base_args(g, subset);
+  q.x = x;
+  q.xscale = reinterpret_cast<const float4*>(x_scale);
+  q.y = rho;
+  q.xout = x;
+  q.bin_factor = bin_factor;
+  q.dt = reinterpret_cast<const float4*>(frame_dt);
+  q.kappa = kappa;
+  q.F = (F_model && beta_kp != 0.f) ? reinterpret_cast<const float4*>(F_model) : nullptr;
+  q.prior_scale = q.F ? beta_kp / ((float)g->S * sigma2) : 0.f;
+  st = launch_back<1>(n_frames / 4, x_type, q, back_rows_max(g), as_stream(stream));
+  if (st) return st;
   KCS_LAUNCHED();
   return KCS_OK;
 }
@@ -671,55 +813,46 @@ int kcs_osl_backproject(const kcs_geometry_t* g, int subset, int n_frames, const
                         float kappa, const float* bin_factor, const float* rho,
                         const float* F_model, float beta_kp, float sigma2, float* x,
                         void* stream) {
+  return kcs_osl_backproject_ex(g, subset, n_frames, frame_dt, kappa, bin_factor, rho, F_model,
+                                beta_kp, sigma2, x, KCS_F32, nullptr, stream);
+}
+
+int kcs_osl_update_ex(const kcs_geometry_t* g, int subset, int n_frames, const float* frame_dt,
+                      float kappa, const void* counts, int counts_type, const float* randoms,
+                      int randoms_layout, const float* bin_factor, const float* F_model,
+                      float beta_kp, float sigma2, void* x, int x_type, const float* x_scale,
+                      void* workspace, size_t ws_bytes, void* stream) {
   clear_error();
   int st = check_geom(g, subset, n_frames);
   if (st) return st;
-  KCS_REQUIRE(subset >= 0, "the OSL update needs a subset index >= 0");
-  KCS_REQUIRE(frame_dt && rho && x, "frame_dt, rho and x must be device pointers");
-  KCS_REQUIRE(kappa > 0.f, "kappa must be positive");
-  KCS_REQUIRE(!F_model || beta_kp == 0.f || sigma2 > 0.f, "sigma2 must be positive");
-  KCS_REQUIRE(aligned16(x) && aligned16(rho) && aligned16(frame_dt) && aligned16(F_model),
-              "arrays must be 16-byte aligned");
-  ProjArgs q = base_args(g, subset);
-  q.x = reinterpret_cast<const float4*>(x);
-  q.y = reinterpret_cast<const float4*>(rho);
-  q.xout = reinterpret_cast<float4*>(x);
-  q.bin_factor = bin_factor;
-  q.dt = reinterpret_cast<const float4*>(frame_dt);
-  q.kappa = kappa;
-  q.F = (F_model && beta_kp != 0.f) ? reinterpret_cast<const float4*>(F_model) : nullptr;
-  q.prior_scale = q.F ? beta_kp / ((float)g->S * sigma2) : 0.f;
-  st = launch_back<1>(n_frames / 4, q, back_rows_max(g), as_stream(stream));
+  KCS_REQUIRE(workspace && ws_bytes >= kcs_osl_workspace_size(g, n_frames),
+              "workspace too small (%zu < %zu)", ws_bytes, kcs_osl_workspace_size(g, n_frames));
+  st = kcs_osl_ratio_ex(g, subset, n_frames, frame_dt, kappa, counts, counts_type, randoms,
+                        randoms_layout, bin_factor, x, x_type, x_scale, workspace, stream);
   if (st) return st;
-  KCS_LAUNCHED();
-  return KCS_OK;
+  return kcs_osl_backproject_ex(g, subset, n_frames, frame_dt, kappa, bin_factor, workspace,
+                                F_model, beta_kp, sigma2, x, x_type, x_scale, stream);
 }
 
 int kcs_osl_update(const kcs_geometry_t* g, int subset, int n_frames, const float* frame_dt,
                    float kappa, const float* counts, const float* randoms, int randoms_layout,
                    const float* bin_factor, const float* F_model, float beta_kp, float sigma2,
                    float* x, void* workspace, size_t ws_bytes, void* stream) {
-  clear_error();
-  int st = check_geom(g, subset, n_frames);
-  if (st) return st;
-  KCS_REQUIRE(workspace && ws_bytes >= kcs_osl_workspace_size(g, n_frames),
-              "workspace too small (%zu < %zu)", ws_bytes, kcs_osl_workspace_size(g, n_frames));
-  float* rho = static_cast<float*>(workspace);
-  st = kcs_osl_ratio(g, subset, n_frames, frame_dt, kappa, counts, randoms, randoms_layout,
-                     bin_factor, x, rho, stream);
-  if (st) return st;
-  return kcs_osl_backproject(g, subset, n_frames, frame_dt, kappa, bin_factor, rho, F_model,
-                             beta_kp, sigma2, x, stream);
+  return kcs_osl_update_ex(g, subset, n_frames, frame_dt, kappa, counts, KCS_F32, randoms,
+                           randoms_layout, bin_factor, F_model, beta_kp, sigma2, x, KCS_F32,
+                           nullptr, workspace, ws_bytes, stream);
 }
 
-int kcs_init_image(const kcs_geometry_t* g, int n_frames, const float* frame_dt, float kappa,
-                   const float* counts, const float* randoms, int randoms_layout,
-                   const float* bin_factor, float* x, void* workspace, size_t ws_bytes,
-                   void* stream) {
+int kcs_init_image_ex(const kcs_geometry_t* g, int n_frames, const float* frame_dt, float kappa,
+                      const void* counts, int counts_type, const float* randoms,
+                      int randoms_layout, const float* bin_factor, void* x, int x_type,
+                      const float* x_scale, void* workspace, size_t ws_bytes, void* stream) {
   clear_error();
   int st = check_geom(g, -1, n_frames);
   if (st) return st;
   KCS_REQUIRE(frame_dt && counts && x, "frame_dt, counts and x must be device pointers");
+  KCS_REQUIRE(storage_ok(x_type), "x_type %d must be KCS_F32, KCS_BF16 or KCS_F16", x_type);
+  KCS_REQUIRE(counts_type == KCS_F32 || counts_type == KCS_U16, "counts_type must be KCS_F32 or KCS_U16");
   KCS_REQUIRE(randoms_layout >= KCS_RANDOMS_NONE && randoms_layout <= KCS_RANDOMS_FULL,
               "bad randoms_layout %d", randoms_layout);
   KCS_REQUIRE(randoms_layout == KCS_RANDOMS_NONE || randoms, "randoms pointer is NULL");
@@ -735,7 +868,10 @@ int kcs_init_image(const kcs_geometry_t* g, int n_frames, const float* frame_dt,
   float* sens = reinterpret_cast<float*>(reinterpret_cast<char*>(cval) + align256(sizeof(float) * 32));
   const long long n_bins_total = (long long)g->nz * g->A * g->B;
   const long long n_vox = (long long)g->nz * g->ny * g->nx;
-  k_partial_sums<<<RED_BLOCKS, 256, 0, s>>>(counts, n_bins_total, M, pc);
+  if (counts_type == KCS_U16)
+    k_partial_sums<<<RED_BLOCKS, 256, 0, s>>>(static_cast<const uint16_t*>(counts), n_bins_total, M, pc);
+  else
+    k_partial_sums<<<RED_BLOCKS, 256, 0, s>>>(static_cast<const float*>(counts), n_bins_total, M, pc);
   KCS_LAUNCHED();
   if (randoms_layout == KCS_RANDOMS_FULL) {
     k_partial_sums<<<RED_BLOCKS, 256, 0, s>>>(randoms, n_bins_total, M, pr);
@@ -745,16 +881,30 @@ int kcs_init_image(const kcs_geometry_t* g, int n_frames, const float* frame_dt,
   p.bin_factor = bin_factor;
   k_sens<<<(unsigned)((n_vox + 255) / 256), 256, 0, s>>>(p, sens);
   KCS_LAUNCHED();
-  k_partial_sums<<<RED_BLOCKS, 256, 0, s>>>(sens, n_vox, 1, ps);
+  k_partial_sums<<<RED_BLOCKS, 256, 0, s>>>(static_cast<const float*>(sens), n_vox, 1, ps);
   KCS_LAUNCHED();
   k_init_fill<<<1, 32, 0, s>>>(pc, randoms_layout == KCS_RANDOMS_FULL ? pr : nullptr, ps,
                                 randoms_layout == KCS_RANDOMS_PER_FRAME, randoms, n_bins_total,
                                 frame_dt, kappa, M, cval);
   KCS_LAUNCHED();
   const long long n = n_vox * M;
-  k_broadcast_frames<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(x, n_vox, M, cval);
+  const unsigned nb = (unsigned)((n + 255) / 256);
+  if (x_type == KCS_BF16)
+    k_broadcast_frames<<<nb, 256, 0, s>>>(static_cast<__nv_bfloat16*>(x), n_vox, M, cval, x_scale);
+  else if (x_type == KCS_F16)
+    k_broadcast_frames<<<nb, 256, 0, s>>>(static_cast<__half*>(x), n_vox, M, cval, x_scale);
+  else
+    k_broadcast_frames<<<nb, 256, 0, s>>>(static_cast<float*>(x), n_vox, M, cval, x_scale);
   KCS_LAUNCHED();
   return KCS_OK;
+}
+
+int kcs_init_image(const kcs_geometry_t* g, int n_frames, const float* frame_dt, float kappa,
+                   const float* counts, const float* randoms, int randoms_layout,
+                   const float* bin_factor, float* x, void* workspace, size_t ws_bytes,
+                   void* stream) {
+  return kcs_init_image_ex(g, n_frames, frame_dt, kappa, counts, KCS_F32, randoms, randoms_layout,
+                           bin_factor, x, KCS_F32, nullptr, workspace, ws_bytes, stream);
 }
 
 }  // extern "C"

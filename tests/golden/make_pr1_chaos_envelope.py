@@ -1,6 +1,6 @@
 """Write pr1_chaos_envelope.json: how far the FP64 oracle's own 5-iteration ICM
 on config PR1 moves when the count calibration kappa is perturbed by 1e-5
-(relative).  ICM with MAP-LM is sensitive to perturbations of the data (LM
+(relative), and when its image and ratio are stored in bfloat16 / float16.  ICM with MAP-LM is sensitive to perturbations of the data (LM
 decisions at the edge of a decrease, voxels switching between local minima),
 so an end-to-end float32 run is judged against this envelope.  Calls only the
 oracle.  Run from the repository root: python tests/golden/make_pr1_chaos_envelope.py
@@ -36,6 +36,22 @@ def main():
     out = {"perturbation": f"kappa x (1 + {EPS:g})", "iterations": 5, "n_lm": 10,
            "image_rel_l2": rel_l2(b[0], a[0]), "model_tac_rel_l2": rel_l2(b[3], a[3]),
            "loglik_rel": abs(ll(b[0]) / ll(a[0]) - 1)}
+    # The same oracle run with the image and ratio stored on the bfloat16 /
+    # float16 grid (per-frame scale = max of the start image): how far storage
+    # rounding alone moves the ICM trajectory.
+    lab = S.labels_pr1()
+    inside = lab > 0
+    out["storage"] = {}
+    for kind in ("bf16", "f16"):
+        c = OI.icm(P["g"], P["counts"], kappa, P["ts"], P["te"], S.FENG, 5, 10, 0.1, 0.1, 0.01,
+                   storage=kind)
+        out["storage"][kind] = {
+            "image_rel_l2": rel_l2(c[0], a[0]), "model_tac_rel_l2": rel_l2(c[3], a[3]),
+            "K1_rel_l2": rel_l2(c[1][0, 0][inside], a[1][0, 0][inside]),
+            "k3_rel_l2": rel_l2(c[1][2, 0][inside], a[1][2, 0][inside]),
+            "Ki_rel_l2": rel_l2(c[2][0][inside], a[2][0][inside]),
+            "Ki_class_mean_rel": max(abs(c[2][0][lab == k].mean() / a[2][0][lab == k].mean() - 1)
+                                     for k in (1, 2, 3))}
     with open(os.path.join(HERE, "pr1_chaos_envelope.json"), "w") as f:
         json.dump(out, f, indent=1)
     print(out)

@@ -69,3 +69,50 @@ def test_mlem_single_voxel_closed_form():
     out = osl.osl_update(g, x, 0, s, 1.0, [1.0])
     ref = 2.0 * (w[0] * 7.0 / (w[0] * 2.0) + w[1] * 5.0 / (w[1] * 2.0)) / (w[0] + w[1])
     np.testing.assert_allclose(out[0, 0, 0, 0], ref, rtol=1e-14)
+
+
+def test_quantize_f16_is_ieee_binary16():
+    rng = np.random.default_rng(7)
+    v = np.concatenate([rng.uniform(0, 2, 5000), 10.0 ** rng.uniform(-9, 5, 5000)])
+    want = np.minimum(v.astype(np.float32), 65504).astype(np.float16).astype(np.float64)
+    got = osl.quantize(v, "f16")
+    # float64 -> binary16 directly and via float32 agree except at double-rounding ties
+    assert np.mean(got == want) > 0.999
+    assert np.all(np.abs(got - want) <= np.spacing(np.float16(np.clip(want, 6.1e-5, 32768))).astype(float))
+    assert osl.quantize(np.array([1e6]), "f16")[0] == 65504.0
+
+
+def test_quantize_bf16_grid_ties_and_bound():
+    # exactly representable values (8 significant bits) are unchanged
+    k = np.arange(128, 256, dtype=np.float64)
+    for e in (-20, -3, 0, 7, 30):
+        v = np.ldexp(k, e)
+        assert np.array_equal(osl.quantize(v, "bf16"), v)
+    # ties go to the even neighbour: 1 + 2^-8 -> 1, 1 + 3 2^-8 -> 1 + 2^-6
+    t = osl.quantize(np.array([1 + 2.0 ** -8, 1 + 3 * 2.0 ** -8, 1 + 2.0 ** -8 + 2.0 ** -30]), "bf16")
+    assert np.array_equal(t, [1.0, 1 + 2.0 ** -6, 1 + 2.0 ** -7])
+    # relative error at most half a unit in the last place (2^-8 relative)
+    rng = np.random.default_rng(8)
+    v = 10.0 ** rng.uniform(-30, 30, 20000)
+    q = osl.quantize(v, "bf16")
+    assert np.all(np.abs(q - v) <= 2.0 ** -8 * v * (1 + 1e-12))
+    # agrees with torch's float32 -> bfloat16 conversion on float32 inputs
+    import torch
+    v32 = v.astype(np.float32)
+    ref = torch.from_numpy(v32).to(torch.bfloat16).to(torch.float64).numpy()
+    assert np.array_equal(osl.quantize(v32.astype(np.float64), "bf16"), ref)
+
+
+def test_stored_update_reduces_to_float64_update_at_fine_grid():
+    g, xt, dt, kappa, r, counts, _ = _setup(S=3, randoms=True)
+    x = osl.initial_image(g, counts, kappa, dt, 2, randoms=r)
+    k = 1
+    ref = osl.osl_update(g, x, k, osl.subset_slice(counts, g, k), kappa, dt, None,
+                         osl.subset_slice(r, g, k))
+    scale = x[0, 0, 0, :]
+    for kind, tol in (("f32", 1e-6), ("f16", 2e-3), ("bf16", 1.6e-2)):
+        got = osl.osl_update_stored(g, osl.quantize(x / scale, kind), k,
+                                    osl.subset_slice(counts, g, k), kappa, dt, scale, kind,
+                                    randoms_k=osl.subset_slice(r, g, k)) * scale
+        err = np.abs(got - ref) / ref
+        assert err.max() < tol, (kind, err.max())
