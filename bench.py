@@ -11,6 +11,11 @@ iteration: 21 x (forward projection + ratio, back-projection + OSL update),
 series (1.44 GB) and the counts (1.06 GB) are larger than the 126 MB L2.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                  [--storage f32|bf16|f16]
+
+--storage bf16 / f16 runs the precision form: image series and ratio
+sinograms stored in bfloat16 / float16 with a per-frame scale (max of the start
+image), counts as uint16; arithmetic stays float32.  The default is float32.
 
 --impl reference times the FP64 CPU oracle on a bounded sample of the same
 workload (one plane, one subset update, one LM step on 4096 voxels) and
@@ -260,20 +265,28 @@ def run_ours(args):
         dist.init_process_group("nccl")
     W, g, kin, dt, kappa, counts, r = build_problem(K, torch, dev, seed=rank, planes=args.planes)
     M = W.n_frames
-    x = K.init_image(g, dt, kappa, counts, r)
+    sdt = {"f32": torch.float32, "bf16": torch.bfloat16, "f16": torch.float16}[args.storage]
+    x_scale = None
+    if args.storage != "f32":
+        assert counts.max().item() < 65536
+        counts = counts.to(torch.uint16)
+        x32 = K.init_image(g, dt, kappa, counts, r)
+        x_scale = x32.reshape(-1, M).amax(0).contiguous()   # max of the start image per frame
+        del x32
+    x = K.init_image(g, dt, kappa, counts, r, dtype=sdt, x_scale=x_scale)
     params = torch.empty((4, W.nz, W.ny, W.nx), device=dev)
     params[:] = torch.tensor(S.XI0, device=dev)[:, None, None, None]
-    F = torch.zeros_like(x)
+    F = torch.zeros(x.shape, device=dev)
     beta_kp = beta_kp_for(kappa)
     st = K.Study(g, kin, dt, kappa, counts, x, params, F=F, randoms=r, n_lm=N_LM,
-                 beta_kp=beta_kp, beta_h=BETA_H, delta=DELTA)
+                 beta_kp=beta_kp, beta_h=BETA_H, delta=DELTA, x_scale=x_scale)
     for _ in range(args.warmup):
         st.iterate(1)
     torch.cuda.synchronize()
 
     # ---- timed region: the kernels icm_iterate issues, with events between them
     S_ = W.n_subsets
-    rhos = {g.n_sub(k): torch.empty(g.sino_shape(M, k), device=dev) for k in range(S_)}
+    rhos = {g.n_sub(k): torch.empty(g.sino_shape(M, k), device=dev, dtype=sdt) for k in range(S_)}
     lm_ws = torch.empty(K.lm_workspace_size(W.nx, W.ny, W.nz), dtype=torch.uint8, device=dev)
 
     def ev():
@@ -284,11 +297,11 @@ def run_ours(args):
     def step(marks):
         for k in range(S_):
             rk = rhos[g.n_sub(k)]
-            K.osl_ratio(g, k, x, dt, kappa, counts, r, out=rk)
+            K.osl_ratio(g, k, x, dt, kappa, counts, r, out=rk, x_scale=x_scale)
             marks.append(("fwd_ratio", ev()))
-            K.osl_backproject(g, k, x, dt, kappa, rk, F=F, beta=beta_kp)
+            K.osl_backproject(g, k, x, dt, kappa, rk, F=F, beta=beta_kp, x_scale=x_scale)
             marks.append(("bwd_osl", ev()))
-        K.map_lm_fit(kin, x, params, N_LM, BETA_H, DELTA, workspace=lm_ws)
+        K.map_lm_fit(kin, x, params, N_LM, BETA_H, DELTA, workspace=lm_ws, x_scale=x_scale)
         marks.append(("lm_step", ev()))
         K.tac_eval(kin, params, out=F)
         marks.append(("tac_eval", ev()))
@@ -317,7 +330,7 @@ def run_ours(args):
     ok = bool(torch.isfinite(params).all().item() and torch.isfinite(x).all().item())
 
     # ---- end to end through the public API with host buffers
-    counts_h = torch.empty(counts.shape, dtype=torch.float32, pin_memory=True)
+    counts_h = torch.empty(counts.shape, dtype=counts.dtype, pin_memory=True)
     counts_h.copy_(counts)
     params_h = torch.empty(params.shape, dtype=torch.float32, pin_memory=True)
     torch.cuda.synchronize()
@@ -337,14 +350,17 @@ def run_ours(args):
     value = world * args.steps / (total_ms / 1e3)
     hbm, smax, src = _peaks()
     V = W.nx * W.ny * W.nz
-    img = V * M * 4
+    es = 4 if args.storage == "f32" else 2                 # stored image / ratio element
+    cs = 4 if args.storage == "f32" else 2                 # counts element
+    img = V * M * es
+    img32 = V * M * 4                                      # F (model TACs) stays float32
     n_sub = W.n_angles // W.n_subsets
-    sino_k = W.nz * n_sub * W.n_bins * M * 4
+    sino_k = W.nz * n_sub * W.n_bins * M
     alg = {  # algorithmic bytes per launch
-        "fwd_ratio": img + 2 * sino_k,            # read x, counts_k; write rho
-        "bwd_osl": sino_k + 3 * img,              # read rho, x, F; write x
-        "lm_step": img + 2 * 4 * V * 4 + 2 * V * 4,   # x; params in/out; lambda in/out
-        "tac_eval": 4 * V * 4 + img,
+        "fwd_ratio": img + sino_k * (cs + es),             # read x, counts_k; write rho
+        "bwd_osl": sino_k * es + 2 * img + img32,          # read rho, x, F; write x
+        "lm_step": img + 2 * 4 * V * 4 + 2 * V * 4,        # x; params in/out; lambda in/out
+        "tac_eval": 4 * V * 4 + img32,
     }
     n_launch = {"fwd_ratio": S_, "bwd_osl": S_, "lm_step": N_LM, "tac_eval": 1}
     kernels = {}
@@ -356,19 +372,20 @@ def run_ours(args):
                          "alg_GB": round(alg[name] / 1e9, 4),
                          "alg_GBps": round(alg[name] / (avg * 1e-3) / 1e9, 1),
                          "frac_hbm": round(alg[name] / (avg * 1e-3) / 1e9 / hbm, 4),
-                         "traffic_GB": _traffic(name)}
+                         "traffic_GB": _traffic(name) if args.storage == "f32" else None}
     dom = max(kernels, key=lambda n: kernels[n]["share"])
     fp32_peak = N_SM * FP32_LANES_PER_SM * 2 * smax * 1e6 / 1e12
     if dom == "lm_step":
         ach = V * LM_FLOPS_PER_VOXEL_STEP / (kernels[dom]["avg_ms"] * 1e-3) / 1e12
         roof = {"bound": "alu", "kernel": dom, "achieved": round(ach, 2),
                 "peak": round(fp32_peak, 1), "unit": "TFLOP/s", "frac": round(ach / fp32_peak, 4),
-                "traffic": _traffic(dom), "traffic_unit": "GB/launch",
+                "traffic": kernels[dom]["traffic_GB"], "traffic_unit": "GB/launch",
                 "peak_source": f"FP32 FMA {N_SM} SM x {FP32_LANES_PER_SM} lanes x 2 x {smax:.0f} MHz"}
     else:
         ach = kernels[dom]["alg_GBps"]
         roof = {"bound": "hbm", "kernel": dom, "achieved": ach, "peak": hbm, "unit": "GB/s",
-                "frac": round(ach / hbm, 4), "traffic": _traffic(dom), "traffic_unit": "GB/launch",
+                "frac": round(ach / hbm, 4), "traffic": kernels[dom]["traffic_GB"],
+                "traffic_unit": "GB/launch",
                 "peak_source": f"{src} hbm_gbs"}
     lm_ms = kernels["lm_step"]["avg_ms"]
     out = {
@@ -378,7 +395,10 @@ def run_ours(args):
         "data": "synthetic",
         "config": {"workload": WORKLOAD if W.nz == 127 else f"{WORKLOAD} [{W.nz} central planes]",
                    "voxels": V, "frames": M, "subsets": S_, "lm_steps": N_LM,
-                   "l2": "inputs larger than L2 (image series 1.44 GB, counts 1.06 GB)",
+                   "l2": f"inputs larger than L2 (image series {img / 1e9:.2f} GB, counts "
+                         f"{W.nz * W.n_angles * W.n_bins * M * cs / 1e9:.2f} GB)",
+                   "storage": ("float32" if args.storage == "f32" else
+                               f"{args.storage} image and ratio with per-frame scale, uint16 counts"),
                    "randoms": "uniform per frame", "beta_kp": beta_kp, "beta_h": BETA_H,
                    "delta": DELTA},
         "roofline": roof,
@@ -388,7 +408,8 @@ def run_ours(args):
         "gpu_launches": args.steps * (2 * S_ + N_LM + 1),
         "clocks": clocks,
         "e2e": {"value": round(world * args.steps / (e2e_ms / 1e3), 4), "unit": "iter/s",
-                "h2d_bytes_per_step": counts.numel() * 4, "d2h_bytes_per_step": params.numel() * 4},
+                "h2d_bytes_per_step": counts.numel() * counts.element_size(),
+                "d2h_bytes_per_step": params.numel() * 4},
         "finite": ok,
     }
     if not args.no_cpu_baseline:
@@ -405,6 +426,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--storage", choices=["f32", "bf16", "f16"], default="f32")
     ap.add_argument("--planes", type=int, default=127,
                     help="central planes of the workload (127 = full; fewer for profiler captures)")
     args = ap.parse_args()
