@@ -284,6 +284,12 @@ int kcs_create_study(kcs_study_t** out, const kcs_study_desc_t* desc);
 int kcs_destroy_study(kcs_study_t* st);
 /* Run n_iter ICM iterations (asynchronous on stream). */
 int kcs_icm_iterate(kcs_study_t* st, int n_iter, void* stream);
+/* Replay the steady-state ICM iteration (prior on) from a CUDA graph recorded
+ * at its first use (enable = 1), or issue every launch from the host (enable =
+ * 0, the default; also releases a recorded graph).  Results are identical;
+ * the graph removes per-launch host cost (Sec. II-D loop, small studies).  The
+ * graph is recorded on a private stream and launched on the caller's stream. */
+int kcs_study_set_graph(kcs_study_t* st, int enable);
 /* Number of ICM iterations issued so far on this study. */
 int kcs_study_iterations(const kcs_study_t* st);
 

@@ -80,6 +80,7 @@ SIGNATURES = {
     "kcs_destroy_study": (i32, [vp]),
     "kcs_icm_iterate": (i32, [vp, i32, vp]),
     "kcs_study_iterations": (i32, [vp]),
+    "kcs_study_set_graph": (i32, [vp, i32]),
 }
 
 for _name, (_res, _args) in SIGNATURES.items():

@@ -289,7 +289,7 @@ class Study:
 
     def __init__(self, geom: Geometry, kin: Kinetics, frame_dt, kappa, counts, x, params, F=None,
                  randoms=None, bin_factor=None, params_given=False, n_lm=10, beta_kp=0.1,
-                 sigma2=1.0, beta_h=0.1, delta=0.01, workspace=None, x_scale=None):
+                 sigma2=1.0, beta_h=0.1, delta=0.01, workspace=None, x_scale=None, graph=False):
         M = kin.M
         dev = x.device
         if F is None:
@@ -319,6 +319,12 @@ class Study:
         h = C.c_void_p()
         check(lib.kcs_create_study(C.byref(h), C.byref(d)))
         self.handle = h
+        if graph:
+            self.set_graph(True)
+
+    def set_graph(self, enable=True):
+        """Replay the steady-state ICM iteration from a CUDA graph."""
+        check(lib.kcs_study_set_graph(self.handle, int(bool(enable))))
 
     def iterate(self, n_iter=1):
         check(lib.kcs_icm_iterate(self.handle, int(n_iter), _stream()))

@@ -2,7 +2,9 @@
 // Compressive Sensing"): (a) one OS-MAP-OSL-KP pass over all subsets with the
 // prior built from the model TACs of the current kinetic maps, then (b) the
 // MAP-LM fit of the maps to the new image series.  Everything is issued on one
-// stream with no host synchronisation.
+// stream with no host synchronisation.  Optionally the steady-state iteration
+// (prior on) is recorded once into a CUDA graph and replayed, which removes the
+// per-launch host cost that dominates small studies.
 
 #include <algorithm>
 
@@ -11,9 +13,60 @@
 struct kcs_study {
   kcs_study_desc_t d;
   int iterations;
+  int use_graph;
+  int device;
+  cudaStream_t cap;       // private stream the steady-state iteration is captured on
+  cudaGraphExec_t exec;   // one ICM iteration with the prior on (null until first use)
 };
 
 using namespace kcs;
+
+namespace {
+
+// (a) one OSL pass over the subsets, (b) the MAP-LM fit, which also refreshes
+// F for the next prior; all on stream s, no host synchronisation.
+int issue_iteration(const kcs_study* st, bool prior, void* stream) {
+  const kcs_study_desc_t& d = st->d;
+  const kcs_geometry* g = d.geom;
+  for (int k = 0; k < g->S; ++k) {
+    const int rc = kcs_osl_update_ex(g, k, d.n_frames, d.frame_dt, d.kappa, d.counts,
+                                     d.counts_type, d.randoms, d.randoms_layout, d.bin_factor,
+                                     prior ? d.F : nullptr, prior ? d.beta_kp : 0.f,
+                                     d.sigma2 > 0.f ? d.sigma2 : 1.f, d.x, d.x_type, d.x_scale,
+                                     d.workspace, d.ws_bytes, stream);
+    if (rc) return rc;
+  }
+  return kcs_map_lm_fit_ex(d.kin, g->nx, g->ny, g->nz, d.x, d.x_type, d.x_scale, d.params,
+                           nullptr, d.n_lm, d.beta_h, d.delta, d.F, d.workspace, d.ws_bytes,
+                           stream);
+}
+
+// Record the steady-state iteration once into a CUDA graph.  Capture runs on a
+// private non-blocking stream (the caller's may be the legacy default stream,
+// which cannot be captured); nothing executes while capturing.
+int build_graph(kcs_study* st) {
+  if (!st->cap) KCS_CUDA(cudaStreamCreateWithFlags(&st->cap, cudaStreamNonBlocking));
+  KCS_CUDA(cudaStreamBeginCapture(st->cap, cudaStreamCaptureModeThreadLocal));
+  const int rc = issue_iteration(st, true, st->cap);
+  cudaGraph_t graph = nullptr;
+  const cudaError_t e = cudaStreamEndCapture(st->cap, &graph);
+  if (rc) {
+    if (graph) cudaGraphDestroy(graph);
+    return rc;
+  }
+  KCS_CUDA(e);
+  const cudaError_t ei = cudaGraphInstantiate(&st->exec, graph, 0);
+  cudaGraphDestroy(graph);
+  KCS_CUDA(ei);
+  return KCS_OK;
+}
+
+void release_graph(kcs_study* st) {
+  if (st->exec) cudaGraphExecDestroy(st->exec);
+  st->exec = nullptr;
+}
+
+}  // namespace
 
 extern "C" {
 
@@ -39,13 +92,29 @@ int kcs_create_study(kcs_study_t** out, const kcs_study_desc_t* d) {
   kcs_study* st = new kcs_study();
   st->d = *d;
   st->iterations = 0;
+  st->use_graph = 0;
+  st->device = d->geom->device;
+  st->cap = nullptr;
+  st->exec = nullptr;
   *out = st;
   return KCS_OK;
 }
 
 int kcs_destroy_study(kcs_study_t* st) {
   clear_error();
+  if (st) {
+    release_graph(st);
+    if (st->cap) cudaStreamDestroy(st->cap);
+  }
   delete st;
+  return KCS_OK;
+}
+
+int kcs_study_set_graph(kcs_study_t* st, int enable) {
+  clear_error();
+  KCS_REQUIRE(st, "study is NULL");
+  st->use_graph = enable ? 1 : 0;
+  if (!enable) release_graph(st);
   return KCS_OK;
 }
 
@@ -56,8 +125,7 @@ int kcs_icm_iterate(kcs_study_t* st, int n_iter, void* stream) {
   KCS_REQUIRE(st, "study is NULL");
   KCS_REQUIRE(n_iter >= 0, "n_iter < 0");
   const kcs_study_desc_t& d = st->d;
-  const kcs_geometry* g = d.geom;
-  const long long V = (long long)g->nz * g->ny * g->nx;
+  const long long V = (long long)d.geom->nz * d.geom->ny * d.geom->nx;
   cudaStream_t s = as_stream(stream);
   for (int it = 0; it < n_iter; ++it) {
     const bool prior = st->iterations > 0 || d.params_given;
@@ -65,18 +133,16 @@ int kcs_icm_iterate(kcs_study_t* st, int n_iter, void* stream) {
       const int rc = launch_tac_eval(d.kin, V, d.params, d.F, nullptr, s);
       if (rc) return rc;
     }
-    for (int k = 0; k < g->S; ++k) {
-      const int rc = kcs_osl_update_ex(g, k, d.n_frames, d.frame_dt, d.kappa, d.counts,
-                                       d.counts_type, d.randoms, d.randoms_layout, d.bin_factor,
-                                       prior ? d.F : nullptr, prior ? d.beta_kp : 0.f,
-                                       d.sigma2 > 0.f ? d.sigma2 : 1.f, d.x, d.x_type, d.x_scale,
-                                       d.workspace, d.ws_bytes, stream);
+    if (prior && st->use_graph) {
+      if (!st->exec) {
+        const int rc = build_graph(st);
+        if (rc) return rc;
+      }
+      KCS_CUDA(cudaGraphLaunch(st->exec, s));
+    } else {
+      const int rc = issue_iteration(st, prior, stream);
       if (rc) return rc;
     }
-    const int rc = kcs_map_lm_fit_ex(d.kin, g->nx, g->ny, g->nz, d.x, d.x_type, d.x_scale,
-                                     d.params, nullptr, d.n_lm, d.beta_h, d.delta, d.F,
-                                     d.workspace, d.ws_bytes, stream);
-    if (rc) return rc;
     st->iterations += 1;
   }
   return KCS_OK;

@@ -96,3 +96,29 @@ def test_pr1_icm_end_to_end(cuda_ok):
     assert e_img < 2 * env["image_rel_l2"]
     assert e_F < 2 * env["model_tac_rel_l2"]
     assert abs(ll_g / ll_r - 1) < 2 * env["loglik_rel"]
+
+
+def test_pr1_graph_replay_identical_and_timed(cuda_ok):
+    """The CUDA-graph replay of the steady-state iteration gives bit-identical
+    results to host-issued launches; prints PR1 iter/s both ways."""
+    K, P, W, kg, kin = _setup()
+    dt = _t(_f32(P["dt"]))
+    kappa = float(np.float32(P["kappa"]))
+    counts = _t(P["counts"])
+    out = {}
+    for graph in (False, True):
+        x = K.init_image(kg, dt, kappa, counts)
+        params = _t(np.broadcast_to(np.array(S.XI0)[:, None, None, None], (4, 1, W.ny, W.nx)))
+        st = K.Study(kg, kin, dt, kappa, counts, x, params, n_lm=10, beta_kp=0.1, beta_h=0.1,
+                     delta=0.01, graph=graph)
+        st.iterate(4)
+        torch.cuda.synchronize()
+        out[graph] = (x.cpu().numpy(), params.cpu().numpy(), st.F.cpu().numpy())
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        st.iterate(50)
+        b.record()
+        torch.cuda.synchronize()
+        print(f"PR1 ICM ({'graph' if graph else 'host-issued'}): {50e3 / a.elapsed_time(b):.0f} iter/s")
+    for u, v in zip(out[False], out[True]):
+        assert np.array_equal(u, v)
