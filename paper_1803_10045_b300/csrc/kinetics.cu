@@ -153,6 +153,13 @@ __device__ __forceinline__ int series_terms(float y) {
 
 // Input-driven series values of one voxel and interval (the derivative
 // channels d1..d3 only when the Jacobian is wanted).
+#ifndef KCS_HORNER_UNROLL
+#define KCS_HORNER_UNROLL 2
+#endif
+#define KCS_PRAGMA(x) _Pragma(#x)
+#define KCS_UNROLL_(n) KCS_PRAGMA(unroll n)
+#define KCS_UNROLL(n) KCS_UNROLL_(n)
+
 struct Series {
   float m1, m2, m3, d1, d2, d3;
 };
@@ -212,7 +219,7 @@ __device__ __forceinline__ void eval_model(const KinDev& kd, const float (&K1)[V
     Series p[VPT];
 #pragma unroll
     for (int v = 0; v < VPT; ++v) p[v] = Series{0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-#pragma unroll 2
+    KCS_UNROLL(KCS_HORNER_UNROLL)
     for (int n = K - 1; n >= 0; --n) {
       const float4* row = tab + (size_t)n * 3 * NCENT;
       float4 c0, c1;
@@ -428,6 +435,9 @@ __global__ void k_huber_grad(int nx, int ny, int nz, const float* p, float delta
 #ifndef KCS_LM_VPT
 #define KCS_LM_VPT 1
 #endif
+#ifndef KCS_LM_CARVEOUT
+#define KCS_LM_CARVEOUT 50   // percent of the maximum shared memory per SM
+#endif
 #ifndef KCS_LM_MINBLOCKS
 #define KCS_LM_MINBLOCKS 8
 #endif
@@ -453,22 +463,31 @@ struct LmArgs {
   float beta, delta;
 };
 
+// Compensated (Kahan) float32 sum: the value is s - c.
+struct KSum {
+  float s, c;
+  __device__ __forceinline__ void add(float v) {
+    const float y = v - c;
+    const float t = s + y;
+    c = (t - s) - y;
+    s = t;
+  }
+};
+
 // Damped normal equations of one voxel, accumulated frame by frame in float32.
 struct Normal {
   float A00, A01, A02, A03, A11, A12, A13, A22, A23, A33;
   float b0, b1, b2, b3;
-  float rr;   // sum of squared residuals at the current point
 };
 
 struct NormalSink {
   const float* xs[LM_VPT];   // the voxels' TACs in shared memory
-  float* fc[LM_VPT];         // their model TACs at the current point (shared memory)
   Normal n[LM_VPT];
+  KSum rr[LM_VPT];           // sum of squared residuals at the current point
   __device__ void operator()(int v, int m, float F, float j0, float j1, float j2, float j3) {
     const float r = xs[v][m] - F;
-    fc[v][m] = F;
+    rr[v].add(r * r);
     Normal& s = n[v];
-    s.rr = fmaf(r, r, s.rr);
     s.A00 = fmaf(j0, j0, s.A00); s.A01 = fmaf(j0, j1, s.A01); s.A02 = fmaf(j0, j2, s.A02);
     s.A03 = fmaf(j0, j3, s.A03); s.A11 = fmaf(j1, j1, s.A11); s.A12 = fmaf(j1, j2, s.A12);
     s.A13 = fmaf(j1, j3, s.A13); s.A22 = fmaf(j2, j2, s.A22); s.A23 = fmaf(j2, j3, s.A23);
@@ -478,59 +497,101 @@ struct NormalSink {
   }
 };
 
-// Change of the data term between the current point (fc) and the trial,
-// 1/2 sum (x - F')^2 - 1/2 sum (x - F)^2 = sum (F - F') (x - (F + F')/2),
-// accumulated directly so that small decreases are not lost in the rounding of
-// two large sums.
-struct DeltaSink {
+// Sum of squared residuals at the trial point.  Both sums are compensated, so
+// their difference resolves objective changes far below the acceptance margin
+// TAU (the rounding of the individual squares is ~6e-8 of the sum), and no
+// per-frame copy of the current model TAC has to be kept.
+struct TrialSink {
   const float* xs[LM_VPT];
-  const float* fc[LM_VPT];
-  float dphi[LM_VPT];
+  KSum rr[LM_VPT];
   __device__ void operator()(int v, int m, float F, float, float, float, float) {
-    const float Fc = fc[v][m];
-    dphi[v] = fmaf(Fc - F, xs[v][m] - 0.5f * (Fc + F), dphi[v]);
+    const float r = xs[v][m] - F;
+    rr[v].add(r * r);
   }
 };
 
-// 1/sqrt(d) in float64 for 1e-30 < d < 1e30: float32 seed, then one
-// Newton-Raphson step r <- r (3 - d r^2) / 2, which squares the seed's relative
-// error (~1e-7 -> ~1e-14).
-__device__ __forceinline__ double rsqrt_nr(double d) {
-  const double r = (double)rsqrtf((float)d);
-  return r * fma(-0.5 * d, r * r, 1.5);
+// Float-float arithmetic for the 4x4 solve: a value is hi + lo with |lo| at
+// most half an ulp of hi (about 48 significant bits).  Built from the
+// error-free sum (Knuth's two-sum) and product (Dekker's, here with a fused
+// multiply-add).  Float64 runs at 1/64 of the float32 rate on this GPU, so the
+// float-float solve costs a small fraction of the float64 one at a precision
+// far beyond that of the float32-accumulated normal equations it solves.
+struct ff {
+  float hi, lo;
+};
+__device__ __forceinline__ ff ff_quick(float a, float b) {   // |a| >= |b|
+  const float s = a + b;
+  return ff{s, b - (s - a)};
+}
+__device__ __forceinline__ ff ff_two_sum(float a, float b) {
+  const float s = a + b;
+  const float bb = s - a;
+  return ff{s, (a - (s - bb)) + (b - bb)};
+}
+__device__ __forceinline__ ff ff_two_prod(float a, float b) {
+  const float p = a * b;
+  return ff{p, fmaf(a, b, -p)};
+}
+__device__ __forceinline__ ff ff_add(ff a, ff b) {
+  const ff s = ff_two_sum(a.hi, b.hi);
+  return ff_quick(s.hi, s.lo + (a.lo + b.lo));
+}
+__device__ __forceinline__ ff ff_sub(ff a, ff b) { return ff_add(a, ff{-b.hi, -b.lo}); }
+__device__ __forceinline__ ff ff_mul(ff a, ff b) {
+  const ff p = ff_two_prod(a.hi, b.hi);
+  return ff_quick(p.hi, fmaf(a.hi, b.lo, fmaf(a.lo, b.hi, p.lo)));
+}
+__device__ __forceinline__ ff ff_mulf(ff a, float b) {
+  const ff p = ff_two_prod(a.hi, b);
+  return ff_quick(p.hi, fmaf(a.lo, b, p.lo));
 }
 
-// Cholesky solve of the damped 4x4 normal equations in float64.  Returns
+// 1/sqrt(d) for 1e-30 < d < 1e30: float seed r, then one Newton step
+// r <- r + r (1 - d r^2) / 2 with the residual 1 - d r^2 formed in float-float,
+// which squares the seed's relative error (~1e-7 -> ~1e-14).
+__device__ __forceinline__ ff ff_rsqrt(ff d) {
+  const float r = rsqrtf(d.hi);
+  const ff e = ff_sub(ff{1.f, 0.f}, ff_mul(d, ff_two_prod(r, r)));
+  return ff_quick(r, 0.5f * r * (e.hi + e.lo));
+}
+
+// Cholesky solve of the damped 4x4 normal equations in float-float.  Returns
 // false (no step) if a pivot is not positive.
-__device__ bool solve4(const Normal& s, double lam, const double rhs[4], double out[4]) {
-  const double A00 = (double)s.A00 + lam, A11 = (double)s.A11 + lam, A22 = (double)s.A22 + lam,
-               A33 = (double)s.A33 + lam;
-  const double A10 = s.A01, A20 = s.A02, A30 = s.A03, A21 = s.A12, A31 = s.A13, A32 = s.A23;
+__device__ bool solve4(const Normal& s, float lam, const ff rhs[4], float out[4]) {
+  const ff A00 = ff_two_sum(s.A00, lam), A11 = ff_two_sum(s.A11, lam),
+           A22 = ff_two_sum(s.A22, lam), A33 = ff_two_sum(s.A33, lam);
   // pivots never exceed their diagonal entry, so bounding the diagonal keeps
-  // every pivot inside the float32 seed's range
-  if (!(A00 < 1e30 && A11 < 1e30 && A22 < 1e30 && A33 < 1e30)) return false;
-  if (!(A00 > 1e-30)) return false;
-  const double i0 = rsqrt_nr(A00);
-  const double L10 = A10 * i0, L20 = A20 * i0, L30 = A30 * i0;
-  const double d1 = A11 - L10 * L10;
-  if (!(d1 > 1e-30)) return false;
-  const double i1 = rsqrt_nr(d1);
-  const double L21 = (A21 - L20 * L10) * i1, L31 = (A31 - L30 * L10) * i1;
-  const double d2 = A22 - L20 * L20 - L21 * L21;
-  if (!(d2 > 1e-30)) return false;
-  const double i2 = rsqrt_nr(d2);
-  const double L32 = (A32 - L30 * L20 - L31 * L21) * i2;
-  const double d3 = A33 - L30 * L30 - L31 * L31 - L32 * L32;
-  if (!(d3 > 1e-30)) return false;
-  const double i3 = rsqrt_nr(d3);
-  const double z0 = rhs[0] * i0;
-  const double z1 = (rhs[1] - L10 * z0) * i1;
-  const double z2 = (rhs[2] - L20 * z0 - L21 * z1) * i2;
-  const double z3 = (rhs[3] - L30 * z0 - L31 * z1 - L32 * z2) * i3;
-  out[3] = z3 * i3;
-  out[2] = (z2 - L32 * out[3]) * i2;
-  out[1] = (z1 - L21 * out[2] - L31 * out[3]) * i1;
-  out[0] = (z0 - L10 * out[1] - L20 * out[2] - L30 * out[3]) * i0;
+  // every pivot, and every square formed below, inside the float range
+  if (!(A00.hi < 1e30f && A11.hi < 1e30f && A22.hi < 1e30f && A33.hi < 1e30f)) return false;
+  if (!(A00.hi > 1e-30f)) return false;
+  const ff i0 = ff_rsqrt(A00);
+  const ff L10 = ff_mulf(i0, s.A01), L20 = ff_mulf(i0, s.A02), L30 = ff_mulf(i0, s.A03);
+  const ff d1 = ff_sub(A11, ff_mul(L10, L10));
+  if (!(d1.hi > 1e-30f)) return false;
+  const ff i1 = ff_rsqrt(d1);
+  const ff L21 = ff_mul(ff_sub(ff{s.A12, 0.f}, ff_mul(L20, L10)), i1);
+  const ff L31 = ff_mul(ff_sub(ff{s.A13, 0.f}, ff_mul(L30, L10)), i1);
+  const ff d2 = ff_sub(ff_sub(A22, ff_mul(L20, L20)), ff_mul(L21, L21));
+  if (!(d2.hi > 1e-30f)) return false;
+  const ff i2 = ff_rsqrt(d2);
+  const ff L32 = ff_mul(ff_sub(ff_sub(ff{s.A23, 0.f}, ff_mul(L30, L20)), ff_mul(L31, L21)), i2);
+  const ff d3 = ff_sub(ff_sub(ff_sub(A33, ff_mul(L30, L30)), ff_mul(L31, L31)), ff_mul(L32, L32));
+  if (!(d3.hi > 1e-30f)) return false;
+  const ff i3 = ff_rsqrt(d3);
+  const ff z0 = ff_mul(rhs[0], i0);
+  const ff z1 = ff_mul(ff_sub(rhs[1], ff_mul(L10, z0)), i1);
+  const ff z2 = ff_mul(ff_sub(ff_sub(rhs[2], ff_mul(L20, z0)), ff_mul(L21, z1)), i2);
+  const ff z3 =
+      ff_mul(ff_sub(ff_sub(ff_sub(rhs[3], ff_mul(L30, z0)), ff_mul(L31, z1)), ff_mul(L32, z2)), i3);
+  const ff o3 = ff_mul(z3, i3);
+  const ff o2 = ff_mul(ff_sub(z2, ff_mul(L32, o3)), i2);
+  const ff o1 = ff_mul(ff_sub(ff_sub(z1, ff_mul(L21, o2)), ff_mul(L31, o3)), i1);
+  const ff o0 =
+      ff_mul(ff_sub(ff_sub(ff_sub(z0, ff_mul(L10, o1)), ff_mul(L20, o2)), ff_mul(L30, o3)), i0);
+  out[0] = o0.hi + o0.lo;
+  out[1] = o1.hi + o1.lo;
+  out[2] = o2.hi + o2.lo;
+  out[3] = o3.hi + o3.lo;
   return true;
 }
 
@@ -560,7 +621,6 @@ __global__ void __launch_bounds__(LM_THREADS, KCS_LM_MINBLOCKS) k_lm_step(LmArgs
   extern __shared__ float xs_all[];
   const int M = L.kd.M;
   const int ld = M + 1;
-  float* fc_all = xs_all + LM_BLOCK_VOX * ld;
   const long long V = (long long)L.nx * L.ny * L.nz;
   const long long v0 = (long long)blockIdx.x * LM_BLOCK_VOX;
   const long long nv = min((long long)LM_BLOCK_VOX, V - v0);
@@ -575,7 +635,7 @@ __global__ void __launch_bounds__(LM_THREADS, KCS_LM_MINBLOCKS) k_lm_step(LmArgs
   bool act[LM_VPT];
   float K1[LM_VPT], k2[LM_VPT], k3[LM_VPT], Vb[LM_VPT];
   NormalSink ns;
-  DeltaSink ds;
+  TrialSink ts;
 #pragma unroll
   for (int k = 0; k < LM_VPT; ++k) {
     const int lv = threadIdx.x + k * LM_THREADS;
@@ -586,11 +646,10 @@ __global__ void __launch_bounds__(LM_THREADS, KCS_LM_MINBLOCKS) k_lm_step(LmArgs
     k3[k] = L.p_in[2 * V + vv[k]];
     Vb[k] = L.p_in[3 * V + vv[k]];
     ns.xs[k] = xs_all + (act[k] ? lv : 0) * ld;
-    ds.xs[k] = ns.xs[k];
-    ns.fc[k] = fc_all + lv * ld;
-    ds.fc[k] = ns.fc[k];
-    ns.n[k] = Normal{0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-    ds.dphi[k] = 0.f;
+    ts.xs[k] = ns.xs[k];
+    ns.n[k] = Normal{0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+    ns.rr[k] = KSum{0.f, 0.f};
+    ts.rr[k] = KSum{0.f, 0.f};
   }
   eval_model<LM_VPT, true>(L.kd, K1, k2, k3, Vb, ns);
   float tr[LM_VPT][4], phi[LM_VPT], Hc[LM_VPT], lam[LM_VPT];
@@ -603,16 +662,18 @@ __global__ void __launch_bounds__(LM_THREADS, KCS_LM_MINBLOCKS) k_lm_step(LmArgs
     const float xi[4] = {K1[k], k2[k], k3[k], Vb[k]};
     float g[4];
     huber_terms(L, V, v, i, j, xi, g, Hc[k]);
-    phi[k] = fmaf(0.5f, ns.n[k].rr, L.beta * Hc[k]);
+    phi[k] = fmaf(0.5f, ns.rr[k].s - ns.rr[k].c, L.beta * Hc[k]);
     lam[k] = L.reset_lambda ? LAMBDA0 : L.lambda[v];
     const Normal& n = ns.n[k];
-    const double rhs[4] = {(double)n.b0 - (double)L.beta * g[0], (double)n.b1 - (double)L.beta * g[1],
-                           (double)n.b2 - (double)L.beta * g[2], (double)n.b3 - (double)L.beta * g[3]};
-    double step[4];
-    solved[k] = solve4(n, (double)lam[k], rhs, step);
+    const float bq[4] = {n.b0, n.b1, n.b2, n.b3};
+    ff rhs[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) rhs[q] = ff_sub(ff{bq[q], 0.f}, ff_two_prod(L.beta, g[q]));
+    float step[4];
+    solved[k] = solve4(n, lam[k], rhs, step);
 #pragma unroll
     for (int q = 0; q < 4; ++q)
-      tr[k][q] = solved[k] ? fminf(fmaxf(xi[q] + (float)step[q], c_lo[q]), c_hi[q]) : xi[q];
+      tr[k][q] = solved[k] ? fminf(fmaxf(xi[q] + step[q], c_lo[q]), c_hi[q]) : xi[q];
   }
   {
     float t1[LM_VPT], t2[LM_VPT], t3[LM_VPT], t4[LM_VPT];
@@ -620,7 +681,7 @@ __global__ void __launch_bounds__(LM_THREADS, KCS_LM_MINBLOCKS) k_lm_step(LmArgs
     for (int k = 0; k < LM_VPT; ++k) {
       t1[k] = tr[k][0]; t2[k] = tr[k][1]; t3[k] = tr[k][2]; t4[k] = tr[k][3];
     }
-    eval_model<LM_VPT, false>(L.kd, t1, t2, t3, t4, ds);
+    eval_model<LM_VPT, false>(L.kd, t1, t2, t3, t4, ts);
   }
 #pragma unroll
   for (int k = 0; k < LM_VPT; ++k) {
@@ -631,7 +692,8 @@ __global__ void __launch_bounds__(LM_THREADS, KCS_LM_MINBLOCKS) k_lm_step(LmArgs
     float gt[4], Ht;
     huber_terms(L, V, v, i, j, tr[k], gt, Ht);
     // Phi(trial) - Phi(current) < -TAU Phi(current)
-    const bool accept = solved[k] && fmaf(L.beta, Ht - Hc[k], ds.dphi[k]) < -TAU * phi[k];
+    const float dphi = 0.5f * ((ts.rr[k].s - ns.rr[k].s) - (ts.rr[k].c - ns.rr[k].c));
+    const bool accept = solved[k] && fmaf(L.beta, Ht - Hc[k], dphi) < -TAU * phi[k];
     const float xi[4] = {K1[k], k2[k], k3[k], Vb[k]};
 #pragma unroll
     for (int q = 0; q < 4; ++q) L.p_out[q * V + v] = accept ? tr[k][q] : xi[q];
@@ -847,10 +909,14 @@ int kcs_map_lm_fit_ex(const kcs_kinetics_t* k, int nx, int ny, int nz, const voi
   L.lambda = lambda ? lambda : lam_ws;
   L.beta = beta_h;
   L.delta = delta;
-  const size_t smem = sizeof(float) * LM_BLOCK_VOX * (k->M + 1) * 2;
+  const size_t smem = sizeof(float) * LM_BLOCK_VOX * (k->M + 1);
   auto kern = x_type == KCS_BF16 ? k_lm_step<__nv_bfloat16>
             : x_type == KCS_F16 ? k_lm_step<__half> : k_lm_step<float>;
   KCS_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  // Ask for the smallest shared-memory carve-out that holds KCS_LM_MINBLOCKS
+  // blocks, leaving the rest of the SM's 256 KB to L1 (coefficient rows).
+  KCS_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                KCS_LM_CARVEOUT));
   const unsigned blocks = (unsigned)((V + LM_BLOCK_VOX - 1) / LM_BLOCK_VOX);
   float* cur = params;
   float* nxt = pong;
