@@ -270,9 +270,7 @@ def run_ours(args):
     if args.storage != "f32":
         assert counts.max().item() < 65536
         counts = counts.to(torch.uint16)
-        x32 = K.init_image(g, dt, kappa, counts, r)
-        x_scale = x32.reshape(-1, M).amax(0).contiguous()   # max of the start image per frame
-        del x32
+        x_scale = K.init_level(g, dt, kappa, counts, r)     # the start image's per-frame level
     x = K.init_image(g, dt, kappa, counts, r, dtype=sdt, x_scale=x_scale)
     params = torch.empty((4, W.nz, W.ny, W.nx), device=dev)
     params[:] = torch.tensor(S.XI0, device=dev)[:, None, None, None]
@@ -419,6 +417,96 @@ def run_ours(args):
         dist.destroy_process_group()
 
 
+# ------------------------------------------------------------------ serving (PR5)
+SERVE_CLASSES = {   # nx, nz, bins, angles, subsets, frame schedule
+    "128x32x12": (128, 32, 128, 96, 8, "pr1"),
+    "256x64x16": (256, 64, 256, 188, 16, "m16"),
+    "344x127x24": (344, 127, 344, 252, 21, "pr2"),
+}
+
+
+def _serve_template(K, torch, name, storage, seed):
+    """One synthetic study of a size class: brain phantom -> model TACs ->
+    projection -> Poisson counts (80 % trues, 20 % uniform randoms), at the
+    count density of the full workload; counts end in pinned host memory."""
+    nx, nz, nb, na, ns, sched = SERVE_CLASSES[name]
+    ts, te = S.schedule(S.SCHEDULES[sched])
+    fov = 344 * 2.09
+    g = K.Geometry(nx, nx, nz, fov / nx, nb, na, fov / nb, ns)
+    kin = K.Kinetics(ts, te, S.FENG)
+    dt = torch.tensor(te - ts, dtype=torch.float32, device="cuda")
+    xi = torch.from_numpy(np.ascontiguousarray(S.phantom_pr2(nx, nz, seed=seed))).cuda()
+    ybar = K.forward_project(g, K.tac_eval(kin, xi))
+    del xi
+    ybar.mul_(dt)
+    W2 = S.WORKLOADS["pr2"]
+    prompts = W2.total_prompts * (nx * nx * nz) / (W2.nx * W2.nx * W2.nz)
+    kappa = float(prompts * (1 - W2.randoms_frac) / ybar.double().sum().item())
+    r = (prompts * W2.randoms_frac) * dt / (dt.sum() * nz * na * nb)
+    ybar.mul_(kappa).add_(r)
+    counts = torch.poisson(ybar, generator=torch.Generator("cuda").manual_seed(seed))
+    del ybar
+    if storage != "f32":
+        counts = counts.to(torch.uint16)
+    host = torch.empty(counts.shape, dtype=counts.dtype, pin_memory=True)
+    host.copy_(counts)
+    return g, kin, dt, kappa, host, r.contiguous()
+
+
+def run_serve(args):
+    """Config PR5: a stream of studies of three sizes with Poisson arrivals
+    served inside an HBM budget (continuous batching at ICM-iteration
+    granularity); reports studies/s and arrival->done latency percentiles."""
+    import torch
+
+    import paper_1803_10045_b300 as K
+    from paper_1803_10045_b300.serving import KcsExecutor, Server, StudyRequest, summarize
+    torch.cuda.set_device(0)
+    tmpl = {n: _serve_template(K, torch, n, args.storage, i)
+            for i, n in enumerate(SERVE_CLASSES)}
+    rng = np.random.default_rng(0)
+    arrivals = np.cumsum(rng.exponential(args.mean_gap, args.requests))
+    arrivals -= arrivals[0]
+    names = list(SERVE_CLASSES)
+    kinds = rng.integers(0, len(names), args.requests)
+    reqs = []
+    for rid, (t, c) in enumerate(zip(arrivals, kinds)):
+        g, kin, dt, kappa, host, r = tmpl[names[c]]
+        reqs.append(StudyRequest(rid, float(t), g, kin, dt, kappa, host, randoms=r,
+                                 n_iter=args.serve_iters, n_lm=N_LM, beta_kp=beta_kp_for(kappa),
+                                 beta_h=BETA_H, delta=DELTA, storage=args.storage))
+    budget = int(args.budget_gb * 1e9)
+    ex = KcsExecutor(budget, args.max_active)
+    torch.cuda.synchronize()
+    sampler = ClockSampler(0)
+    sampler.start()
+    srv = Server(ex, budget, args.max_active)
+    recs = srv.run(reqs)
+    torch.cuda.synchronize()
+    clocks = sampler.stop()
+    summ = summarize(recs)
+    per = {}
+    for rec, c in zip(recs, kinds):
+        if rec.status == "done":
+            per.setdefault(names[c], []).append(rec.latency)
+    print(json.dumps({
+        "metric": "studies/s (PR5 serving)", "value": round(summ["studies_per_s"], 4),
+        "unit": "studies/s", "n_gpus": 1, "higher_is_better": True,
+        "p50_s": round(summ["p50_s"], 3), "p99_s": round(summ["p99_s"], 3),
+        "completed": summ["completed"], "rejected": summ["rejected"],
+        "makespan_s": round(summ["makespan_s"], 2), "dtype": "f32", "data": "synthetic",
+        "config": {"workload": "PR5: Poisson arrivals, sizes 128^2x32x12 / 256^2x64x16 / "
+                               "344^2x127x24 uniformly, ICM x 10 LM steps each",
+                   "requests": args.requests, "mean_gap_s": args.mean_gap,
+                   "storage": args.storage, "budget_gb": args.budget_gb,
+                   "max_active": args.max_active, "icm_iterations": args.serve_iters,
+                   "peak_arena_gb": round(srv.arena.peak / 1e9, 2),
+                   "class_counts": {n: int((kinds == i).sum()) for i, n in enumerate(names)}},
+        "latency_by_class_p50_s": {n: round(float(np.percentile(v, 50)), 3)
+                                   for n, v in per.items()},
+        "clocks": clocks}))
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -429,8 +517,17 @@ def main():
     ap.add_argument("--storage", choices=["f32", "bf16", "f16"], default="f32")
     ap.add_argument("--planes", type=int, default=127,
                     help="central planes of the workload (127 = full; fewer for profiler captures)")
+    ap.add_argument("--serve", action="store_true",
+                    help="config PR5: serve a Poisson stream of studies of three sizes")
+    ap.add_argument("--requests", type=int, default=200)
+    ap.add_argument("--mean-gap", type=float, default=0.5)
+    ap.add_argument("--budget-gb", type=float, default=32.0)
+    ap.add_argument("--max-active", type=int, default=16)
+    ap.add_argument("--serve-iters", type=int, default=10)
     args = ap.parse_args()
-    if args.impl == "reference":
+    if args.serve:
+        run_serve(args)
+    elif args.impl == "reference":
         run_reference(args)
     else:
         run_ours(args)

@@ -161,6 +161,13 @@ int kcs_init_image(const kcs_geometry_t* g, int n_frames, const float* frame_dt,
                    const float* counts, const float* randoms, int randoms_layout,
                    const float* bin_factor, float* x, void* workspace, size_t ws_bytes,
                    void* stream);
+/* The per-frame levels c_m of that start image into level [M] (device float),
+ * without writing an image: the natural per-frame scale of the precision form
+ * (the start image is then stored as exactly 1). */
+int kcs_init_level(const kcs_geometry_t* g, int n_frames, const float* frame_dt, float kappa,
+                   const void* counts, int counts_type, const float* randoms, int randoms_layout,
+                   const float* bin_factor, float* level, void* workspace, size_t ws_bytes,
+                   void* stream);
 /* Precision form: counts as counts_type; x written as x_type holding c_m / x_scale[m]. */
 int kcs_init_image_ex(const kcs_geometry_t* g, int n_frames, const float* frame_dt, float kappa,
                       const void* counts, int counts_type, const float* randoms,

@@ -188,6 +188,25 @@ def osl_backproject(g: Geometry, subset, x, frame_dt, kappa, rho, bin_factor=Non
     return x
 
 
+def init_level(g: Geometry, frame_dt, kappa, counts, randoms=None, bin_factor=None,
+               workspace=None, out=None):
+    """Per-frame level c_m [M] of the uniform start image (the precision form's
+    natural per-frame scale)."""
+    M = counts.shape[-1]
+    pr, layout = _randoms(g, randoms, M)
+    ct = _storage(counts, (F32, U16), "counts")
+    if out is None:
+        out = torch.empty(M, device=counts.device, dtype=torch.float32)
+    if workspace is None:
+        workspace = _workspace(osl_workspace_size(g, M), counts.device)
+    check(lib.kcs_init_level(
+        g.handle, M, _ptr(frame_dt, "frame_dt", (M,)), float(kappa),
+        _ptr(counts, "counts", g.sino_shape(M), dtype=counts.dtype), ct, pr, layout,
+        _ptr(bin_factor, "bin_factor", (g.nz, g.n_angles, g.n_bins), allow_none=True),
+        _ptr(out, "level", (M,)), C.c_void_p(workspace.data_ptr()), workspace.numel(), _stream()))
+    return out
+
+
 def init_image(g: Geometry, frame_dt, kappa, counts, randoms=None, bin_factor=None, out=None,
                workspace=None, dtype=torch.float32, x_scale=None):
     """Uniform per-frame start image matching the measured trues (stored as

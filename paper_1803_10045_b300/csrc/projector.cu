@@ -843,29 +843,29 @@ int kcs_osl_update(const kcs_geometry_t* g, int subset, int n_frames, const floa
                            nullptr, workspace, ws_bytes, stream);
 }
 
-int kcs_init_image_ex(const kcs_geometry_t* g, int n_frames, const float* frame_dt, float kappa,
+}  // extern "C"
+
+// Per-frame level c_m of the uniform start image into cval [M] (device).
+static int init_level(const kcs_geometry_t* g, int n_frames, const float* frame_dt, float kappa,
                       const void* counts, int counts_type, const float* randoms,
-                      int randoms_layout, const float* bin_factor, void* x, int x_type,
-                      const float* x_scale, void* workspace, size_t ws_bytes, void* stream) {
-  clear_error();
+                      int randoms_layout, const float* bin_factor, float* cval, void* workspace,
+                      size_t ws_bytes, cudaStream_t s) {
   int st = check_geom(g, -1, n_frames);
   if (st) return st;
-  KCS_REQUIRE(frame_dt && counts && x, "frame_dt, counts and x must be device pointers");
-  KCS_REQUIRE(storage_ok(x_type), "x_type %d must be KCS_F32, KCS_BF16 or KCS_F16", x_type);
+  KCS_REQUIRE(frame_dt && counts && cval, "frame_dt, counts and the output must be device pointers");
   KCS_REQUIRE(counts_type == KCS_F32 || counts_type == KCS_U16, "counts_type must be KCS_F32 or KCS_U16");
   KCS_REQUIRE(randoms_layout >= KCS_RANDOMS_NONE && randoms_layout <= KCS_RANDOMS_FULL,
               "bad randoms_layout %d", randoms_layout);
   KCS_REQUIRE(randoms_layout == KCS_RANDOMS_NONE || randoms, "randoms pointer is NULL");
   KCS_REQUIRE(kappa > 0.f, "kappa must be positive");
   KCS_REQUIRE(workspace && ws_bytes >= kcs_osl_workspace_size(g, n_frames), "workspace too small");
-  cudaStream_t s = as_stream(stream);
   const int M = n_frames;
   char* w = static_cast<char*>(workspace);
   double* pc = reinterpret_cast<double*>(w);
   double* pr = pc + (size_t)RED_BLOCKS * M;
   double* ps = reinterpret_cast<double*>(w + align256(sizeof(double) * RED_BLOCKS * (2 * (size_t)M + 1)));
-  float* cval = reinterpret_cast<float*>(reinterpret_cast<char*>(ps) + align256(sizeof(double) * RED_BLOCKS));
-  float* sens = reinterpret_cast<float*>(reinterpret_cast<char*>(cval) + align256(sizeof(float) * 32));
+  float* sens = reinterpret_cast<float*>(reinterpret_cast<char*>(ps) + align256(sizeof(double) * RED_BLOCKS) +
+                                         align256(sizeof(float) * 32));
   const long long n_bins_total = (long long)g->nz * g->A * g->B;
   const long long n_vox = (long long)g->nz * g->ny * g->nx;
   if (counts_type == KCS_U16)
@@ -887,6 +887,38 @@ int kcs_init_image_ex(const kcs_geometry_t* g, int n_frames, const float* frame_
                                 randoms_layout == KCS_RANDOMS_PER_FRAME, randoms, n_bins_total,
                                 frame_dt, kappa, M, cval);
   KCS_LAUNCHED();
+  return KCS_OK;
+}
+
+extern "C" {
+
+int kcs_init_level(const kcs_geometry_t* g, int n_frames, const float* frame_dt, float kappa,
+                   const void* counts, int counts_type, const float* randoms, int randoms_layout,
+                   const float* bin_factor, float* level, void* workspace, size_t ws_bytes,
+                   void* stream) {
+  clear_error();
+  return init_level(g, n_frames, frame_dt, kappa, counts, counts_type, randoms, randoms_layout,
+                    bin_factor, level, workspace, ws_bytes, as_stream(stream));
+}
+
+int kcs_init_image_ex(const kcs_geometry_t* g, int n_frames, const float* frame_dt, float kappa,
+                      const void* counts, int counts_type, const float* randoms,
+                      int randoms_layout, const float* bin_factor, void* x, int x_type,
+                      const float* x_scale, void* workspace, size_t ws_bytes, void* stream) {
+  clear_error();
+  KCS_REQUIRE(x, "x must be a device pointer");
+  KCS_REQUIRE(storage_ok(x_type), "x_type %d must be KCS_F32, KCS_BF16 or KCS_F16", x_type);
+  cudaStream_t s = as_stream(stream);
+  KCS_REQUIRE(g && workspace, "NULL geometry or workspace");
+  char* w = static_cast<char*>(workspace);
+  float* cval = reinterpret_cast<float*>(
+      w + align256(sizeof(double) * RED_BLOCKS * (2 * (size_t)n_frames + 1)) +
+      align256(sizeof(double) * RED_BLOCKS));
+  const int st = init_level(g, n_frames, frame_dt, kappa, counts, counts_type, randoms,
+                            randoms_layout, bin_factor, cval, workspace, ws_bytes, s);
+  if (st) return st;
+  const int M = n_frames;
+  const long long n_vox = (long long)g->nz * g->ny * g->nx;
   const long long n = n_vox * M;
   const unsigned nb = (unsigned)((n + 255) / 256);
   if (x_type == KCS_BF16)
