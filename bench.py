@@ -480,7 +480,7 @@ def run_serve(args):
     torch.cuda.synchronize()
     sampler = ClockSampler(0)
     sampler.start()
-    srv = Server(ex, budget, args.max_active)
+    srv = Server(ex, budget, args.max_active, policy=args.policy)
     recs = srv.run(reqs)
     torch.cuda.synchronize()
     clocks = sampler.stop()
@@ -500,6 +500,7 @@ def run_serve(args):
                    "requests": args.requests, "mean_gap_s": args.mean_gap,
                    "storage": args.storage, "budget_gb": args.budget_gb,
                    "max_active": args.max_active, "icm_iterations": args.serve_iters,
+                   "policy": args.policy,
                    "peak_arena_gb": round(srv.arena.peak / 1e9, 2),
                    "class_counts": {n: int((kinds == i).sum()) for i, n in enumerate(names)}},
         "latency_by_class_p50_s": {n: round(float(np.percentile(v, 50)), 3)
@@ -524,6 +525,7 @@ def main():
     ap.add_argument("--budget-gb", type=float, default=32.0)
     ap.add_argument("--max-active", type=int, default=16)
     ap.add_argument("--serve-iters", type=int, default=10)
+    ap.add_argument("--policy", choices=["fifo", "backfill"], default="fifo")
     args = ap.parse_args()
     if args.serve:
         run_serve(args)

@@ -105,9 +105,18 @@ class Server:
     """
 
     def __init__(self, executor, budget_bytes, max_active=8, clock: Callable[[], float] = None,
-                 idle_sleep=50e-6):
+                 idle_sleep=50e-6, policy="fifo", max_bypass=64):
+        """policy "fifo": strict first come first served (a study that does not
+        fit blocks those behind it).  policy "backfill": when the oldest study
+        does not fit, later ones that fit are admitted, each bypass of the
+        oldest counted; once it has been bypassed max_bypass times nothing else
+        is admitted before it (no starvation)."""
+        if policy not in ("fifo", "backfill"):
+            raise ValueError(policy)
         self.ex = executor
         self.arena = Arena(budget_bytes)
+        self.policy = policy
+        self.max_bypass = int(max_bypass)
         self.max_active = int(max_active)
         self.clock = clock or time.perf_counter
         self.idle_sleep = idle_sleep
@@ -124,6 +133,7 @@ class Server:
         queue = collections.deque()
         active = []                         # [req, job, offset, slot, phase]
         free_slots = list(range(self.max_active))[::-1]
+        bypassed = {}                       # rid -> times a later study was admitted first
         t0 = self.clock()
         i = 0
         while i < len(reqs) or queue or active:
@@ -143,18 +153,26 @@ class Server:
                     else:
                         keep.append(r)
                 queue = keep
-            # admission: first come first served while the budget and a slot allow
-            while queue and free_slots:
-                r = queue[0]
+            # admission while the budget and a slot allow
+            k = 0
+            while k < len(queue) and free_slots:
+                r = queue[k]
                 rec = recs[r.rid]
                 if rec.footprint > self.arena.size:
-                    queue.popleft()
+                    del queue[k]
                     rec.status, rec.done = "rejected", now
                     continue
+                if k > 0 and bypassed.get(queue[0].rid, 0) >= self.max_bypass:
+                    break                   # the oldest study has waited long enough
                 off = self.arena.alloc(rec.footprint)
                 if off is None:
-                    break
-                queue.popleft()
+                    if self.policy == "fifo":
+                        break
+                    k += 1                  # backfill: try a later, smaller study
+                    continue
+                del queue[k]
+                if k > 0:
+                    bypassed[queue[0].rid] = bypassed.get(queue[0].rid, 0) + 1
                 slot = free_slots.pop()
                 job = self.ex.admit(r, off, slot)
                 rec.status, rec.admitted = "active", now

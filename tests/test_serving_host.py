@@ -147,3 +147,28 @@ def test_cancel_queued_and_active():
     assert [r.status for r in recs] == ["cancelled", "done", "cancelled"]
     assert 0 < recs[0].iterations < 50 and recs[2].iterations == 0
     assert srv.arena.used == 0 and ex.concurrent == 0
+
+
+def test_backfill_admits_small_behind_a_blocked_large_one():
+    ex = FakeExecutor(lag=2)
+    # a resident large study, then a large one that must wait, then small ones
+    reqs = [FakeReq(0, 0.0, 700 * ALIGN, 40), FakeReq(1, 0.0005, 700 * ALIGN, 5)] + \
+        [FakeReq(2 + i, 0.0006, 100 * ALIGN, 3) for i in range(4)]
+    fifo = Server(FakeExecutor(lag=2), 1000 * ALIGN, clock=FakeClock(), idle_sleep=0).run(reqs)
+    back = Server(ex, 1000 * ALIGN, clock=FakeClock(), idle_sleep=0, policy="backfill").run(reqs)
+    assert all(r.status == "done" for r in fifo + back)
+    # FIFO: the small studies wait for the blocked large one; backfill: they run
+    # beside the first large study and finish before the second is admitted
+    assert all(f.done > fifo[1].admitted for f in fifo[2:])
+    assert all(b.done < back[1].admitted for b in back[2:])
+
+
+def test_backfill_does_not_starve_the_oldest():
+    reqs = [FakeReq(0, 0.0, 600 * ALIGN, 30), FakeReq(1, 0.0005, 600 * ALIGN, 2)] + \
+        [FakeReq(2 + i, 0.0006 + 0.0001 * i, 300 * ALIGN, 2) for i in range(60)]
+    srv = Server(FakeExecutor(lag=1), 1000 * ALIGN, clock=FakeClock(), idle_sleep=0,
+                 policy="backfill", max_bypass=5)
+    recs = srv.run(reqs)
+    assert all(r.status == "done" for r in recs)
+    bypassers = [r for r in recs[2:] if r.admitted < recs[1].admitted]
+    assert len(bypassers) <= 5
