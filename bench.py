@@ -52,11 +52,29 @@ KAPPA_PR1 = 5.06e-3
 def beta_kp_for(kappa):
     return 0.1 * kappa / KAPPA_PR1
 FP32_LANES_PER_SM, N_SM = 128, 148
-# Nominal float32 FLOPs of one MAP-LM voxel-step on this workload: 15 Horner
-# channels x 2 flop x (sum over the 24 intervals of K = 12 + ceil(2.72 a D) at
-# a = 0.19: 330 terms), 24 frames x (2 x 25 recursion + 2 x 15 normal-equation)
-# flop, and ~400 flop of Huber terms and step logic.
-LM_FLOPS_PER_VOXEL_STEP = 2 * 15 * 330 + 24 * (2 * 25 + 2 * 15) + 400
+
+
+def _series_terms(y):
+    """Series length per interval for y = delta D (delta = a - centre)."""
+    return int(np.ceil(2 * y + 5.75 * np.sqrt(y) + 3.75))
+
+
+def lm_flops_per_voxel_step(interval_lengths, a=0.19, frames=24):
+    """Nominal float32 flops (FMA = 2) of one MAP-LM voxel-step at k2 + k3 = a
+    (grey matter; centre 0, delta = a): Horner sums of the Jacobian pass (6
+    channels) and the trial pass (3 channels) over every interval, the
+    input-free channels (4 + 2) once per distinct interval length, the state
+    recursion per interval (~30 + 12 flop), per frame the model, residual and
+    normal equations (~70 flop), ~100 flop for the 4x4 solve and ~384 for the
+    Huber terms of the current and trial points."""
+    K = [_series_terms(a * D) for D in interval_lengths]
+    Kd = [_series_terms(a * D) for D in sorted(set(interval_lengths))]
+    return (9 * 2 * sum(K) + 6 * 2 * sum(Kd) + 42 * len(interval_lengths) + 70 * frames
+            + 100 + 384)
+
+
+_TS, _TE = S.schedule(S.SCHEDULES["pr2"])
+LM_FLOPS_PER_VOXEL_STEP = lm_flops_per_voxel_step(list(_TE - _TS), frames=len(_TE))
 
 
 # DRAM traffic (read + write) per launch measured by ncu on the 16-central-plane
@@ -64,9 +82,9 @@ LM_FLOPS_PER_VOXEL_STEP = 2 * 15 * 330 + 24 * (2 * 25 + 2 * 15) + 400
 # planes: every kernel touches each plane's data independently), valid while
 # the kernel's source file is unchanged (sha256 prefix); see profiles/.
 TRAFFIC = {
-    "lm_step": {"bytes": 247.36e6 * 127 / 16, "src": "kinetics.cu", "sha": "cd58f0be38e22b87"},
-    "bwd_osl": {"bytes": 505.94e6 * 127 / 16, "src": "projector.cu", "sha": "66b4b2a2b0f15b26"},
-    "fwd_ratio": {"bytes": 237.46e6 * 127 / 16, "src": "projector.cu", "sha": "66b4b2a2b0f15b26"},
+    "lm_step": {"bytes": 247.35e6 * 127 / 16, "src": "kinetics.cu", "sha": "d7ce4d016a7eaac9"},
+    "bwd_osl": {"bytes": 505.97e6 * 127 / 16, "src": "projector.cu", "sha": "a749aa18841896d1"},
+    "fwd_ratio": {"bytes": 259.76e6 * 127 / 16, "src": "projector.cu", "sha": "a749aa18841896d1"},
 }
 
 
