@@ -526,6 +526,92 @@ def run_serve(args):
         "clocks": clocks}))
 
 
+# ------------------------------------------------------------------ MC bias/variance
+def run_mc(args):
+    """Bias and variance of the kinetic maps over many noise realisations of
+    config PR1 for the three methods of Sec. IV-A (INDIRECT: OSEM then a
+    post-reconstruction fit; DIRECT: ICM without the spatial prior; KCS: the
+    full ICM), as a function of the number of iterations.  The realisations
+    are stacked as planes of one study (planes are independent through the
+    whole path), so one launch sequence reconstructs all of them; the start
+    level is pooled over the realisations."""
+    import torch
+
+    import paper_1803_10045_b300 as K
+    torch.cuda.set_device(0)
+    W = S.WORKLOADS[args.mc_workload]
+    R = args.realisations
+    ts, te = W.frames()
+    g = K.Geometry(W.nx, W.ny, R, W.vox_mm, W.n_bins, W.n_angles, W.bin_mm, W.n_subsets)
+    kin = K.Kinetics(ts, te, S.FENG)
+    dt = torch.tensor(te - ts, dtype=torch.float32, device="cuda")
+    paper = args.mc_workload == "paper"
+    xi1 = S.phantom_paper(W.nx) if paper else S.phantom_pr1(W.nx)    # [4][1][ny][nx]
+    truth = torch.from_numpy(np.ascontiguousarray(np.repeat(xi1, R, axis=1))).float().cuda()
+    ybar = K.forward_project(g, K.tac_eval(kin, truth)) * dt    # every plane the same
+    for trues in [float(t) for t in args.mc_trues.split(",")]:
+        for beta_kp in [float(b) for b in args.mc_beta_kp.split(",")]:
+            _mc_case(args, K, torch, W, R, g, kin, dt, ybar, xi1, paper, trues, beta_kp)
+
+
+def _mc_case(args, K, torch, W, R, g, kin, dt, ybar, xi1, paper, trues, beta_kp):
+    M = W.n_frames
+    kappa = float(trues / ybar[0].double().sum().item())
+    counts = torch.poisson(ybar * kappa, generator=torch.Generator("cuda").manual_seed(args.seed))
+    checkpoints = sorted({int(c) for c in args.mc_iters.split(",")})
+    lab = S.labels_paper(W.nx) if paper else S.labels_pr1(W.nx)
+    classes = ({"inner": 3, "middle": 2, "outer": 1} if paper     # blood (K1 = 0) excluded
+               else {"gm": 2, "wm": 3, "bg": 1})
+    xi_np = xi1[:, 0]
+    ki_true = xi_np[0] * xi_np[2] / np.maximum(xi_np[1] + xi_np[2], 1e-12)
+    start = torch.tensor(S.XI0, dtype=torch.float32, device="cuda")
+
+    def stats(params):
+        p = params.double().cpu().numpy()                       # [4][R][ny][nx]
+        ki = p[0] * p[2] / np.maximum(p[1] + p[2], 1e-12)
+        out = {}
+        for cname, code in classes.items():
+            m = lab == code
+            for pname, est, tru in (("K1", p[0], xi_np[0]), ("k3", p[2], xi_np[2]),
+                                    ("Ki", ki, ki_true)):
+                e = est[:, m]                                   # [R][voxels]
+                t = tru[m]
+                out[f"{cname}_{pname}"] = {
+                    "bias_pct": round(100 * float(np.mean((e.mean(0) - t) / t)), 3),
+                    "std_pct": round(100 * float(np.mean(e.std(0, ddof=1) / t)), 3)}
+        return out
+
+    result = {}
+    t0 = time.perf_counter()
+    for method in ("indirect", "direct", "kcs"):
+        x = K.init_image(g, dt, kappa, counts)
+        params = torch.empty((4, R, W.ny, W.nx), device="cuda")
+        params[:] = start[:, None, None, None]
+        st = K.Study(g, kin, dt, kappa, counts, x, params, n_lm=N_LM, beta_kp=beta_kp,
+                     beta_h=BETA_H, delta=DELTA, method=method)
+        done = 0
+        result[method] = {}
+        for c in checkpoints:
+            st.iterate(c - done)
+            done = c
+            if method == "indirect":
+                params[:] = start[:, None, None, None]
+                st.fit(N_LM)
+            torch.cuda.synchronize()
+            result[method][str(c)] = stats(params)
+    wall = time.perf_counter() - t0
+    print(json.dumps({
+        "metric": f"MC bias/std of kinetic maps ({args.mc_workload})", "unit": "% of the true value",
+        "realisations": R, "checkpoints": checkpoints, "seed": args.seed,
+        "config": {"workload": (f"{args.mc_workload}: 64x64, {M} frames, 96 bins x 90 angles, "
+                                f"4 subsets, {trues:g} trues per realisation, beta_kp "
+                                f"{beta_kp:g}, beta_h 0.1 (KCS), delta 0.01, 10 LM steps per "
+                                "iteration"),
+                   "trues": trues, "beta_kp": beta_kp,
+                   "wall_s": round(wall, 2)},
+        "results": result}))
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -544,8 +630,18 @@ def main():
     ap.add_argument("--max-active", type=int, default=16)
     ap.add_argument("--serve-iters", type=int, default=10)
     ap.add_argument("--policy", choices=["fifo", "backfill"], default="fifo")
+    ap.add_argument("--mc", action="store_true",
+                    help="bias/variance of INDIRECT, DIRECT and KCS over PR1 noise realisations")
+    ap.add_argument("--realisations", type=int, default=100)
+    ap.add_argument("--mc-iters", default="1,2,5,10,20")
+    ap.add_argument("--mc-workload", choices=["pr1", "paper"], default="pr1")
+    ap.add_argument("--mc-trues", default="1e6", help="comma-separated expected trues per realisation")
+    ap.add_argument("--mc-beta-kp", default="0.1", help="comma-separated kinetics-prior weights")
+    ap.add_argument("--seed", type=int, default=0)
     args = ap.parse_args()
-    if args.serve:
+    if args.mc:
+        run_mc(args)
+    elif args.serve:
         run_serve(args)
     elif args.impl == "reference":
         run_reference(args)

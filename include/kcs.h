@@ -207,8 +207,13 @@ int kcs_ki(int64_t n_vox, const float* params, float* ki, void* stream);
  * over the in-plane 3x3 clique (Eq. 6, Sec. II-C), per map: [4][Z][ny][nx]. */
 int kcs_huber_grad(int nx, int ny, int nz, const float* params, float delta, float* grad,
                    void* stream);
+/* The same with a choice of neighbourhood: 8 (the in-plane 3x3 clique above)
+ * or 26 (the 3x3x3 cube: a 3D variant the paper does not use; it couples
+ * adjacent planes, so plane sharding then needs a one-plane halo). */
+int kcs_huber_grad_nb(int nx, int ny, int nz, const float* params, float delta,
+                      int neighbourhood, float* grad, void* stream);
 /* n_steps synchronous MAP-LM steps (Eq. 4) of every voxel's TAC x [Z][ny][nx][M]:
- *   (J^T J + lambda I) step = J^T (x - F) - beta_h dH/dxi      (solved in float64)
+ *   (J^T J + lambda I) step = J^T (x - F) - beta_h dH/dxi  (float-float Cholesky)
  *   trial = clamp(xi + step, 0, (2, 2, 1, 1)); accept iff the voxel objective
  *   Phi = 1/2 |x - F|^2 + beta_h sum_p sum_{N8} huber(xi_p - xi_{k,p}) falls by
  *   more than 1e-5 Phi, with the neighbours frozen at their start-of-step values;
@@ -222,11 +227,17 @@ int kcs_map_lm_fit(const kcs_kinetics_t* k, int nx, int ny, int nz, const float*
                    float* F_out, void* workspace, size_t ws_bytes, void* stream);
 /* Precision form: the image TACs x stored as x_type (KCS_F32/BF16/F16) with
  * per-frame scale x_scale [M] (NULL = 1); the fit itself is unchanged (float32
- * model, float64 4x4 solve). */
+ * model, float-float 4x4 solve). */
 int kcs_map_lm_fit_ex(const kcs_kinetics_t* k, int nx, int ny, int nz, const void* x,
                       int x_type, const float* x_scale, float* params, float* lambda,
                       int n_steps, float beta_h, float delta, float* F_out, void* workspace,
                       size_t ws_bytes, void* stream);
+/* kcs_map_lm_fit_ex with the Huber neighbourhood as in kcs_huber_grad_nb
+ * (8 or 26). */
+int kcs_map_lm_fit_nb(const kcs_kinetics_t* k, int nx, int ny, int nz, const void* x,
+                      int x_type, const float* x_scale, float* params, float* lambda,
+                      int n_steps, float beta_h, float delta, int neighbourhood, float* F_out,
+                      void* workspace, size_t ws_bytes, void* stream);
 
 /* ------------------------------------------------- MAP-LM without allocation
  * The paper has no counterpart to this entry point; it exists for callers that
@@ -284,7 +295,18 @@ typedef struct kcs_study_desc {
   int counts_type;
   int x_type;
   const float* x_scale;
+  /* reconstruction method (Sec. IV-A; zero-initialised = KCS):
+   *   KCS_METHOD_KCS      the ICM above (kinetics prior + Huber MAP-LM),
+   *   KCS_METHOD_DIRECT   the same without the spatial prior (beta_h taken as 0),
+   *   KCS_METHOD_INDIRECT each iteration is an OSEM pass (no prior, no fit);
+   *                       the kinetic fit runs once, after the reconstruction,
+   *                       in kcs_study_fit (post-reconstruction fitting). */
+  int method;
+  /* Huber neighbourhood of the fit: 0 or 8 = in-plane 3x3 (Sec. II-C), 26 = 3x3x3 */
+  int neighbourhood;
 } kcs_study_desc_t;
+
+enum { KCS_METHOD_KCS = 0, KCS_METHOD_DIRECT = 1, KCS_METHOD_INDIRECT = 2 };
 
 size_t kcs_study_workspace_size(const kcs_geometry_t* g, int n_frames);
 int kcs_create_study(kcs_study_t** out, const kcs_study_desc_t* desc);
@@ -297,6 +319,11 @@ int kcs_icm_iterate(kcs_study_t* st, int n_iter, void* stream);
  * the graph removes per-launch host cost (Sec. II-D loop, small studies).  The
  * graph is recorded on a private stream and launched on the caller's stream. */
 int kcs_study_set_graph(kcs_study_t* st, int enable);
+/* n_steps MAP-LM steps on the study's current image from its current maps
+ * (lambda reset to 1e-2), then F <- F(params): the post-reconstruction fit of
+ * KCS_METHOD_INDIRECT (beta_h taken as 0 for INDIRECT and DIRECT).
+ * Asynchronous on stream. */
+int kcs_study_fit(kcs_study_t* st, int n_steps, void* stream);
 /* Number of ICM iterations issued so far on this study. */
 int kcs_study_iterations(const kcs_study_t* st);
 

@@ -87,6 +87,9 @@ class Workload:
 
 WORKLOADS = {
     "pr1": Workload("pr1", 64, 1, 2.0, 96, 90, 2.0, 4, "pr1", 1.0e6, 0.0),
+    # the paper's own simulation (Sec. IV-A): its 24-frame scheme and the
+    # concentric phantom with a central blood square, on the PR1 geometry
+    "paper": Workload("paper", 64, 1, 2.0, 96, 90, 2.0, 4, "paper", 1.0e6, 0.0),
     "pr2": Workload("pr2", 344, 127, 2.09, 344, 252, 2.09, 21, "pr2", 2.0e8, 0.2),
 }
 
@@ -114,6 +117,41 @@ def phantom_pr1(n=64):
     for code, cls in ((1, "bg"), (2, "gm"), (3, "wm")):
         for p in range(4):
             xi[p, 0][lab == code] = CLASS_XI[cls][p]
+    return xi
+
+
+# Table I of the paper, read in the printed column order (f_v, K1, k2, k3) with
+# f_v as a fraction (the blood row's 1.0 is pure blood); stored as (K1, k2, k3, Vb).
+TABLE1_XI = {
+    "blood": (0.0, 0.0, 0.0, 1.0),
+    "inner": (0.75, 0.35, 0.031, 0.13),
+    "middle": (0.62, 0.30, 0.026, 0.116),
+    "outer": (0.51, 0.27, 0.018, 0.0985),
+}
+
+
+def labels_paper(n=64):
+    """Label map [ny][nx] of the paper's geometrical phantom (its figure is not
+    available; reading: three concentric discs and a central blood square):
+    0 outside, 1 outer disc r = 0.44 n, 2 middle r = 0.31 n, 3 inner r = 0.19 n,
+    4 blood square of side n / 8."""
+    lab = np.zeros((n, n), np.int8)
+    lab[_ellipse(n, n, 0.44 * n, 0.44 * n)] = 1
+    lab[_ellipse(n, n, 0.31 * n, 0.31 * n)] = 2
+    lab[_ellipse(n, n, 0.19 * n, 0.19 * n)] = 3
+    h = n // 16
+    c = n // 2
+    lab[c - h:c + h, c - h:c + h] = 4
+    return lab
+
+
+def phantom_paper(n=64):
+    """Kinetic maps [4][1][n][n] float64 of the paper's phantom with Table I values."""
+    lab = labels_paper(n)
+    xi = np.zeros((4, 1, n, n))
+    for code, region in ((1, "outer"), (2, "middle"), (3, "inner"), (4, "blood")):
+        for p in range(4):
+            xi[p, 0][lab == code] = TABLE1_XI[region][p]
     return xi
 
 

@@ -11,6 +11,10 @@ Iteration n:
      lambda reset to 1e-2.
 Outputs: image series x, kinetic maps xi, Ki map, and F(xi).
 
+The three methods compared in Sec. IV-A: INDIRECT (OSEM, then a
+post-reconstruction fit), DIRECT (the ICM without the spatial prior in the
+fit) and KCS DIRECT (the full ICM).
+
 ICM on this joint objective is not convex and the paper defines no stopping
 rule, so parity is on the trajectory for fixed iteration counts.
 """
@@ -23,10 +27,18 @@ from . import kinetics, lm, osl
 
 def icm(geom, counts, kappa, t_start, t_end, feng, n_iter, n_lm,
         beta_kp, beta_h, delta, x0=None, xi0=None, xi_start=(0.05, 0.10, 0.03, 0.03),
-        bin_factor=None, randoms=None, sigma2=1.0, storage=None):
+        bin_factor=None, randoms=None, sigma2=1.0, storage=None, method="kcs", nbhd="2d"):
     """storage = None runs in float64 throughout; storage = "bf16" or "f16"
     holds the image (and each subset's ratio sinogram) on that grid with the
-    per-frame scale max_v x_vm of the start image (osl.osl_update_stored)."""
+    per-frame scale max_v x_vm of the start image (osl.osl_update_stored).
+
+    method (Sec. IV-A): "kcs" as above; "direct" the same with beta_h = 0 (no
+    spatial prior in the fit); "indirect" n_iter OSEM passes (no prior, no fit)
+    followed by one post-reconstruction fit of n_lm steps with beta_h = 0."""
+    if method not in ("kcs", "direct", "indirect"):
+        raise ValueError(method)
+    if method != "kcs":
+        beta_h = 0.0
     dt = np.asarray(t_end) - np.asarray(t_start)
     Z = counts.shape[0]
     x = osl.initial_image(geom, counts, kappa, dt, Z, bin_factor, randoms) if x0 is None else x0.copy()
@@ -38,7 +50,7 @@ def icm(geom, counts, kappa, t_start, t_end, feng, n_iter, n_lm,
         np.asarray(xi_start, float)[:, None, None, None], (4, Z, geom.ny, geom.nx)).copy()
     for n in range(n_iter):
         F = None
-        if n > 0 or have_xi:
+        if method != "indirect" and (n > 0 or have_xi):
             F = kinetics.model_maps(xi, t_start, t_end, feng)
         if storage is None:
             x = osl.osl_pass(geom, x, counts, kappa, dt, bin_factor, randoms, F, beta_kp, sigma2)
@@ -50,6 +62,9 @@ def icm(geom, counts, kappa, t_start, t_end, feng, n_iter, n_lm,
                     osl.subset_slice(bin_factor, geom, k), osl.subset_slice(randoms, geom, k),
                     F, beta_kp, sigma2)
             x = xs * scale
-        xi, _ = lm.lm_fit(x, xi, n_lm, t_start, t_end, feng, beta_h, delta)
+        if method != "indirect":
+            xi, _ = lm.lm_fit(x, xi, n_lm, t_start, t_end, feng, beta_h, delta, nbhd=nbhd)
+    if method == "indirect":
+        xi, _ = lm.lm_fit(x, xi, n_lm, t_start, t_end, feng, beta_h, delta, nbhd=nbhd)
     F = kinetics.model_maps(xi, t_start, t_end, feng)
     return x, xi, kinetics.ki(xi), F

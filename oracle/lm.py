@@ -11,7 +11,8 @@ takes the standard Huber function they approximate:
     psi(t) = h'(t) = clamp(t, -delta, delta)
 
 Neighbourhood: the 3x3 in-plane clique of Sec. II-C (8 neighbours, unit
-weights, neighbours outside the image skipped, no coupling between planes).
+weights, neighbours outside the image skipped, no coupling between planes);
+optionally (nbhd = "3d") the 26 neighbours of the 3x3x3 cube, unit weights.
 One delta and one beta serve all four maps.
 
     H_v(xi) = sum_p sum_{k in N8(v)} h(xi_p - xi_{k,p})
@@ -49,6 +50,8 @@ LAMBDA0 = 1e-2
 LAMBDA_MIN, LAMBDA_MAX = 1e-7, 1e7
 TAU = 1e-5          # relative objective decrease required to accept a trial
 NEIGHBOURS = [(dy, dx) for dy in (-1, 0, 1) for dx in (-1, 0, 1) if (dy, dx) != (0, 0)]
+NEIGHBOURS_3D = [(dz, dy, dx) for dz in (-1, 0, 1) for dy in (-1, 0, 1) for dx in (-1, 0, 1)
+                 if (dz, dy, dx) != (0, 0, 0)]
 
 
 def huber(t, delta):
@@ -74,26 +77,52 @@ def _shifted(maps, dy, dx):
     return out, valid
 
 
-def huber_grad(maps, delta):
+def _shifted3(maps, dz, dy, dx):
+    """Neighbour values maps[:, z+dz, j+dy, i+dx] and a validity mask [Z][Y][X]."""
+    Z = maps.shape[1]
+    out = np.zeros_like(maps)
+    valid = np.zeros(maps.shape[1:], bool)
+    zs = slice(max(0, -dz), Z - max(0, dz))
+    zn = slice(max(0, dz), Z - max(0, -dz))
+    nb, v2 = _shifted(maps[:, zn], dy, dx)
+    out[:, zs] = nb
+    valid[zs] = v2
+    return out, valid
+
+
+def _neighbours(maps, nbhd):
+    """(neighbour values, validity) for every offset of the neighbourhood:
+    "2d" the 8 in-plane neighbours of Sec. II-C, "3d" the 26 of the 3x3x3 cube
+    (unit weights, neighbours outside the volume skipped)."""
+    if nbhd == "2d":
+        for dy, dx in NEIGHBOURS:
+            nb, valid = _shifted(maps, dy, dx)
+            yield nb, np.broadcast_to(valid, maps.shape[1:])
+    elif nbhd == "3d":
+        for dz, dy, dx in NEIGHBOURS_3D:
+            yield _shifted3(maps, dz, dy, dx)
+    else:
+        raise ValueError(nbhd)
+
+
+def huber_grad(maps, delta, nbhd="2d"):
     """dH/dxi for maps [4][Z][Y][X] -> [4][Z][Y][X]."""
     g = np.zeros_like(maps, dtype=np.float64)
-    for dy, dx in NEIGHBOURS:
-        nb, valid = _shifted(maps, dy, dx)
+    for nb, valid in _neighbours(maps, nbhd):
         g += np.where(valid, psi(maps - nb, delta), 0.0)
     return g
 
 
-def huber_local(trial, maps, delta):
+def huber_local(trial, maps, delta, nbhd="2d"):
     """H_v evaluated at per-voxel values trial [4][Z][Y][X] against frozen maps."""
     e = np.zeros(maps.shape[1:])
-    for dy, dx in NEIGHBOURS:
-        nb, valid = _shifted(maps, dy, dx)
+    for nb, valid in _neighbours(maps, nbhd):
         e += np.where(valid, huber(trial - nb, delta).sum(axis=0), 0.0)
     return e
 
 
 def lm_step(x, maps, lam, t_start, t_end, feng, beta, delta,
-            lo=(0, 0, 0, 0), hi=(2, 2, 1, 1)):
+            lo=(0, 0, 0, 0), hi=(2, 2, 1, 1), nbhd="2d"):
     """One synchronous MAP-LM step for all voxels.
 
     x [Z][Y][X][M] image TACs, maps [4][Z][Y][X], lam [Z][Y][X].
@@ -105,8 +134,8 @@ def lm_step(x, maps, lam, t_start, t_end, feng, beta, delta,
     xv = x.reshape(-1, M)
     F, J = kinetics.model(xi, t_start, t_end, feng)
     r = xv - F
-    phi = 0.5 * np.sum(r * r, axis=1) + beta * huber_local(maps, maps, delta).ravel()
-    g = huber_grad(maps, delta).reshape(4, -1).T
+    phi = 0.5 * np.sum(r * r, axis=1) + beta * huber_local(maps, maps, delta, nbhd).ravel()
+    g = huber_grad(maps, delta, nbhd).reshape(4, -1).T
     A = np.einsum("vmi,vmj->vij", J, J) + lam.ravel()[:, None, None] * np.eye(4)
     rhs = np.einsum("vmi,vm->vi", J, r) - beta * g
     L = np.linalg.cholesky(A)
@@ -115,7 +144,7 @@ def lm_step(x, maps, lam, t_start, t_end, feng, beta, delta,
     Ft = kinetics.model(trial, t_start, t_end, feng, jacobian=False)
     rt = xv - Ft
     trial_maps = trial.T.reshape(maps.shape)
-    phi_t = 0.5 * np.sum(rt * rt, axis=1) + beta * huber_local(trial_maps, maps, delta).ravel()
+    phi_t = 0.5 * np.sum(rt * rt, axis=1) + beta * huber_local(trial_maps, maps, delta, nbhd).ravel()
     acc = (phi_t - phi) < -TAU * phi
     new = np.where(acc[:, None], trial, xi)
     lam_new = np.where(acc, np.maximum(lam.ravel() / 10, LAMBDA_MIN),
@@ -125,10 +154,11 @@ def lm_step(x, maps, lam, t_start, t_end, feng, beta, delta,
             phi_new.reshape(sh))
 
 
-def lm_fit(x, maps, n_steps, t_start, t_end, feng, beta, delta, lam=None, **box):
-    """n_steps synchronous MAP-LM steps; lambda starts at 1e-2 unless given."""
+def lm_fit(x, maps, n_steps, t_start, t_end, feng, beta, delta, lam=None, **kw):
+    """n_steps synchronous MAP-LM steps; lambda starts at 1e-2 unless given
+    (kw: the box lo/hi and the neighbourhood nbhd of lm_step)."""
     if lam is None:
         lam = np.full(maps.shape[1:], LAMBDA0)
     for _ in range(n_steps):
-        maps, lam, _, _ = lm_step(x, maps, lam, t_start, t_end, feng, beta, delta, **box)
+        maps, lam, _, _ = lm_step(x, maps, lam, t_start, t_end, feng, beta, delta, **kw)
     return maps, lam

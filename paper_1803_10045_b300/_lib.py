@@ -42,7 +42,7 @@ class StudyDesc(C.Structure):
                 ("x", vp), ("params", vp), ("F", vp), ("params_given", i32), ("n_lm", i32),
                 ("beta_kp", f32), ("sigma2", f32), ("beta_h", f32), ("delta", f32),
                 ("workspace", vp), ("ws_bytes", sz), ("counts_type", i32), ("x_type", i32),
-                ("x_scale", vp)]
+                ("x_scale", vp), ("method", i32), ("neighbourhood", i32)]
 
 
 SIGNATURES = {
@@ -65,6 +65,9 @@ SIGNATURES = {
                                 vp, vp, sz, vp]),
     "kcs_init_level": (i32, [vp, i32, vp, f32, vp, i32, vp, i32, vp, vp, vp, sz, vp]),
     "kcs_init_image_ex": (i32, [vp, i32, vp, f32, vp, i32, vp, i32, vp, vp, i32, vp, vp, sz, vp]),
+    "kcs_huber_grad_nb": (i32, [i32, i32, i32, vp, f32, i32, vp, vp]),
+    "kcs_map_lm_fit_nb": (i32, [vp, i32, i32, i32, vp, i32, vp, vp, vp, i32, f32, f32, i32, vp, vp,
+                                sz, vp]),
     "kcs_map_lm_fit_ex": (i32, [vp, i32, i32, i32, vp, i32, vp, vp, vp, i32, f32, f32, vp, vp, sz,
                                 vp]),
     "kcs_create_kinetics": (i32, [pp, i32, dp, dp, dp, vp]),
@@ -82,6 +85,7 @@ SIGNATURES = {
     "kcs_icm_iterate": (i32, [vp, i32, vp]),
     "kcs_study_iterations": (i32, [vp]),
     "kcs_study_set_graph": (i32, [vp, i32]),
+    "kcs_study_fit": (i32, [vp, i32, vp]),
 }
 
 for _name, (_res, _args) in SIGNATURES.items():

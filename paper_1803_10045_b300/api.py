@@ -16,6 +16,7 @@ from ._lib import StudyDesc, check, lib
 
 RANDOMS_NONE, RANDOMS_PER_FRAME, RANDOMS_FULL = 0, 1, 2
 F32, BF16, F16, U16 = 0, 1, 2, 3
+METHODS = {"kcs": 0, "direct": 1, "indirect": 2}
 _STORAGE = {torch.float32: F32, torch.bfloat16: BF16, torch.float16: F16, torch.uint16: U16}
 
 
@@ -274,11 +275,12 @@ def ki(params):
     return out
 
 
-def huber_grad(params, delta):
+def huber_grad(params, delta, neighbourhood=8):
+    """dH/dxi of maps [4][Z][Y][X] over 8 in-plane or 26 (3x3x3) neighbours."""
     _, nz, ny, nx = params.shape
     out = torch.empty_like(params)
-    check(lib.kcs_huber_grad(nx, ny, nz, _ptr(params, "params"), float(delta), _ptr(out, "grad"),
-                             _stream()))
+    check(lib.kcs_huber_grad_nb(nx, ny, nz, _ptr(params, "params"), float(delta),
+                                int(neighbourhood), _ptr(out, "grad"), _stream()))
     return out
 
 
@@ -287,19 +289,19 @@ def lm_workspace_size(nx, ny, nz):
 
 
 def map_lm_fit(kin: Kinetics, x, params, n_steps, beta_h, delta, lam=None, F_out=None,
-               workspace=None, x_scale=None):
+               workspace=None, x_scale=None, neighbourhood=8):
     """n_steps MAP-LM steps on params [4][Z][Y][X] (in place) for TACs x [Z][Y][X][M]
     (x float32, bfloat16 or float16 holding x / x_scale[m])."""
     nz, ny, nx, M = x.shape
     xt = _storage(x, (F32, BF16, F16), "x")
     if workspace is None:
         workspace = _workspace(lm_workspace_size(nx, ny, nz), x.device)
-    check(lib.kcs_map_lm_fit_ex(
+    check(lib.kcs_map_lm_fit_nb(
         kin.handle, nx, ny, nz, _ptr(x, "x", (nz, ny, nx, M), dtype=x.dtype), xt,
         _ptr(x_scale, "x_scale", (M,), allow_none=True), _ptr(params, "params", (4, nz, ny, nx)),
         _ptr(lam, "lambda", (nz, ny, nx), allow_none=True), int(n_steps), float(beta_h), float(delta),
-        _ptr(F_out, "F_out", (nz, ny, nx, M), allow_none=True), C.c_void_p(workspace.data_ptr()),
-        workspace.numel(), _stream()))
+        int(neighbourhood), _ptr(F_out, "F_out", (nz, ny, nx, M), allow_none=True),
+        C.c_void_p(workspace.data_ptr()), workspace.numel(), _stream()))
     return params
 
 
@@ -308,7 +310,8 @@ class Study:
 
     def __init__(self, geom: Geometry, kin: Kinetics, frame_dt, kappa, counts, x, params, F=None,
                  randoms=None, bin_factor=None, params_given=False, n_lm=10, beta_kp=0.1,
-                 sigma2=1.0, beta_h=0.1, delta=0.01, workspace=None, x_scale=None, graph=False):
+                 sigma2=1.0, beta_h=0.1, delta=0.01, workspace=None, x_scale=None, graph=False,
+                 method="kcs", neighbourhood=8):
         M = kin.M
         dev = x.device
         if F is None:
@@ -335,6 +338,10 @@ class Study:
         d.params_given, d.n_lm = int(bool(params_given)), int(n_lm)
         d.beta_kp, d.sigma2, d.beta_h, d.delta = float(beta_kp), float(sigma2), float(beta_h), float(delta)
         d.workspace, d.ws_bytes = C.c_void_p(workspace.data_ptr()), workspace.numel()
+        if method not in METHODS:
+            raise ValueError(f"method must be one of {sorted(METHODS)}")
+        d.method = METHODS[method]
+        d.neighbourhood = int(neighbourhood)
         h = C.c_void_p()
         check(lib.kcs_create_study(C.byref(h), C.byref(d)))
         self.handle = h
@@ -347,6 +354,10 @@ class Study:
 
     def iterate(self, n_iter=1):
         check(lib.kcs_icm_iterate(self.handle, int(n_iter), _stream()))
+
+    def fit(self, n_steps):
+        """Post-reconstruction kinetic fit of the current image (INDIRECT)."""
+        check(lib.kcs_study_fit(self.handle, int(n_steps), _stream()))
 
     @property
     def iterations(self):

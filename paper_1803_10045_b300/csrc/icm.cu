@@ -25,9 +25,15 @@ namespace {
 
 // (a) one OSL pass over the subsets, (b) the MAP-LM fit, which also refreshes
 // F for the next prior; all on stream s, no host synchronisation.
+// Huber weight of the fit: the spatial prior is part of KCS only.
+float fit_beta_h(const kcs_study_desc_t& d) { return d.method == KCS_METHOD_KCS ? d.beta_h : 0.f; }
+int fit_nbhd(const kcs_study_desc_t& d) { return d.neighbourhood == 26 ? 26 : 8; }
+
 int issue_iteration(const kcs_study* st, bool prior, void* stream) {
   const kcs_study_desc_t& d = st->d;
   const kcs_geometry* g = d.geom;
+  const bool indirect = d.method == KCS_METHOD_INDIRECT;
+  if (indirect) prior = false;
   for (int k = 0; k < g->S; ++k) {
     const int rc = kcs_osl_update_ex(g, k, d.n_frames, d.frame_dt, d.kappa, d.counts,
                                      d.counts_type, d.randoms, d.randoms_layout, d.bin_factor,
@@ -36,9 +42,10 @@ int issue_iteration(const kcs_study* st, bool prior, void* stream) {
                                      d.workspace, d.ws_bytes, stream);
     if (rc) return rc;
   }
-  return kcs_map_lm_fit_ex(d.kin, g->nx, g->ny, g->nz, d.x, d.x_type, d.x_scale, d.params,
-                           nullptr, d.n_lm, d.beta_h, d.delta, d.F, d.workspace, d.ws_bytes,
-                           stream);
+  if (indirect) return KCS_OK;
+  return kcs_map_lm_fit_nb(d.kin, g->nx, g->ny, g->nz, d.x, d.x_type, d.x_scale, d.params,
+                           nullptr, d.n_lm, fit_beta_h(d), d.delta, fit_nbhd(d), d.F, d.workspace,
+                           d.ws_bytes, stream);
 }
 
 // Record the steady-state iteration once into a CUDA graph.  Capture runs on a
@@ -86,6 +93,11 @@ int kcs_create_study(kcs_study_t** out, const kcs_study_desc_t* d) {
               "x_type %d must be KCS_F32, KCS_BF16 or KCS_F16", d->x_type);
   KCS_REQUIRE(d->counts_type == KCS_F32 || d->counts_type == KCS_U16,
               "counts_type %d must be KCS_F32 or KCS_U16", d->counts_type);
+  KCS_REQUIRE(d->method == KCS_METHOD_KCS || d->method == KCS_METHOD_DIRECT ||
+                  d->method == KCS_METHOD_INDIRECT,
+              "method %d must be KCS_METHOD_KCS, _DIRECT or _INDIRECT", d->method);
+  KCS_REQUIRE(d->neighbourhood == 0 || d->neighbourhood == 8 || d->neighbourhood == 26,
+              "neighbourhood %d must be 0, 8 or 26", d->neighbourhood);
   KCS_REQUIRE(d->workspace && d->ws_bytes >= kcs_study_workspace_size(d->geom, d->n_frames),
               "workspace too small (%zu < %zu)", d->ws_bytes,
               kcs_study_workspace_size(d->geom, d->n_frames));
@@ -120,6 +132,17 @@ int kcs_study_set_graph(kcs_study_t* st, int enable) {
 
 int kcs_study_iterations(const kcs_study_t* st) { return st ? st->iterations : -1; }
 
+int kcs_study_fit(kcs_study_t* st, int n_steps, void* stream) {
+  clear_error();
+  KCS_REQUIRE(st, "study is NULL");
+  KCS_REQUIRE(n_steps >= 0, "n_steps < 0");
+  const kcs_study_desc_t& d = st->d;
+  const kcs_geometry* g = d.geom;
+  return kcs_map_lm_fit_nb(d.kin, g->nx, g->ny, g->nz, d.x, d.x_type, d.x_scale, d.params,
+                           nullptr, n_steps, fit_beta_h(d), d.delta, fit_nbhd(d), d.F,
+                           d.workspace, d.ws_bytes, stream);
+}
+
 int kcs_icm_iterate(kcs_study_t* st, int n_iter, void* stream) {
   clear_error();
   KCS_REQUIRE(st, "study is NULL");
@@ -128,7 +151,7 @@ int kcs_icm_iterate(kcs_study_t* st, int n_iter, void* stream) {
   const long long V = (long long)d.geom->nz * d.geom->ny * d.geom->nx;
   cudaStream_t s = as_stream(stream);
   for (int it = 0; it < n_iter; ++it) {
-    const bool prior = st->iterations > 0 || d.params_given;
+    const bool prior = (st->iterations > 0 || d.params_given) && d.method != KCS_METHOD_INDIRECT;
     if (prior && st->iterations == 0) {
       const int rc = launch_tac_eval(d.kin, V, d.params, d.F, nullptr, s);
       if (rc) return rc;

@@ -413,21 +413,29 @@ __device__ __forceinline__ float huber_h(float t, float d) {
   return at <= d ? 0.5f * t * t : fmaf(d, at, -0.5f * d * d);
 }
 
-__global__ void k_huber_grad(int nx, int ny, int nz, const float* p, float delta, float* g) {
+// nb3d = 0: the 8 in-plane neighbours (Sec. II-C); 1: the 26 of the 3x3x3 cube.
+__global__ void k_huber_grad(int nx, int ny, int nz, const float* p, float delta, int nb3d,
+                             float* g) {
   const long long n = (long long)nx * ny * nz;
   const long long v = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (v >= n) return;
   const int i = (int)(v % nx);
   const int j = (int)((v / nx) % ny);
+  const int k = (int)(v / ((long long)nx * ny));
+  const int dz0 = nb3d ? -1 : 0, dz1 = nb3d ? 1 : 0;
   float acc[4] = {0.f, 0.f, 0.f, 0.f};
-  for (int dy = -1; dy <= 1; ++dy)
-    for (int dx = -1; dx <= 1; ++dx) {
-      if (!dx && !dy) continue;
-      const int ii = i + dx, jj = j + dy;
-      if (ii < 0 || ii >= nx || jj < 0 || jj >= ny) continue;
-      const long long u = v + (long long)dy * nx + dx;
-      for (int q = 0; q < 4; ++q) acc[q] += huber_psi(p[q * n + v] - p[q * n + u], delta);
-    }
+  for (int dz = dz0; dz <= dz1; ++dz) {
+    const int kk = k + dz;
+    if (kk < 0 || kk >= nz) continue;
+    for (int dy = -1; dy <= 1; ++dy)
+      for (int dx = -1; dx <= 1; ++dx) {
+        if (!dx && !dy && !dz) continue;
+        const int ii = i + dx, jj = j + dy;
+        if (ii < 0 || ii >= nx || jj < 0 || jj >= ny) continue;
+        const long long u = v + ((long long)dz * ny + dy) * nx + dx;
+        for (int q = 0; q < 4; ++q) acc[q] += huber_psi(p[q * n + v] - p[q * n + u], delta);
+      }
+  }
   for (int q = 0; q < 4; ++q) g[q * n + v] = acc[q];
 }
 
@@ -461,6 +469,7 @@ struct LmArgs {
   float* lambda;         // [V]
   int reset_lambda;
   float beta, delta;
+  int nb3d;              // Huber neighbourhood: 0 in-plane 3x3, 1 the 3x3x3 cube
 };
 
 // Compensated (Kahan) float32 sum: the value is s - c.
@@ -598,22 +607,27 @@ __device__ bool solve4(const Normal& s, float lam, const ff rhs[4], float out[4]
 // Huber gradient of a voxel and the potential of a given point against the
 // frozen neighbours.
 __device__ __forceinline__ void huber_terms(const LmArgs& L, long long V, long long v, int i, int j,
-                                            const float (&pt)[4], float (&g)[4], float& H) {
+                                            int k, const float (&pt)[4], float (&g)[4], float& H) {
   g[0] = g[1] = g[2] = g[3] = 0.f;
   H = 0.f;
-  for (int dy = -1; dy <= 1; ++dy)
-    for (int dx = -1; dx <= 1; ++dx) {
-      if (!dx && !dy) continue;
-      const int ii = i + dx, jj = j + dy;
-      if (ii < 0 || ii >= L.nx || jj < 0 || jj >= L.ny) continue;
-      const long long u = v + (long long)dy * L.nx + dx;
+  const int dz0 = L.nb3d ? -1 : 0, dz1 = L.nb3d ? 1 : 0;
+  for (int dz = dz0; dz <= dz1; ++dz) {
+    const int kk = k + dz;
+    if (kk < 0 || kk >= L.nz) continue;
+    for (int dy = -1; dy <= 1; ++dy)
+      for (int dx = -1; dx <= 1; ++dx) {
+        if (!dx && !dy && !dz) continue;
+        const int ii = i + dx, jj = j + dy;
+        if (ii < 0 || ii >= L.nx || jj < 0 || jj >= L.ny) continue;
+        const long long u = v + ((long long)dz * L.ny + dy) * L.nx + dx;
 #pragma unroll
-      for (int q = 0; q < 4; ++q) {
-        const float t = pt[q] - __ldg(L.p_in + q * V + u);
-        g[q] += huber_psi(t, L.delta);
-        H += huber_h(t, L.delta);
+        for (int q = 0; q < 4; ++q) {
+          const float t = pt[q] - __ldg(L.p_in + q * V + u);
+          g[q] += huber_psi(t, L.delta);
+          H += huber_h(t, L.delta);
+        }
       }
-    }
+  }
 }
 
 template <class TX>
@@ -659,9 +673,10 @@ __global__ void __launch_bounds__(LM_THREADS, KCS_LM_MINBLOCKS) k_lm_step(LmArgs
     const long long v = vv[k];
     const int i = (int)(v % L.nx);
     const int j = (int)((v / L.nx) % L.ny);
+    const int z = (int)(v / ((long long)L.nx * L.ny));
     const float xi[4] = {K1[k], k2[k], k3[k], Vb[k]};
     float g[4];
-    huber_terms(L, V, v, i, j, xi, g, Hc[k]);
+    huber_terms(L, V, v, i, j, z, xi, g, Hc[k]);
     phi[k] = fmaf(0.5f, ns.rr[k].s - ns.rr[k].c, L.beta * Hc[k]);
     lam[k] = L.reset_lambda ? LAMBDA0 : L.lambda[v];
     const Normal& n = ns.n[k];
@@ -689,8 +704,9 @@ __global__ void __launch_bounds__(LM_THREADS, KCS_LM_MINBLOCKS) k_lm_step(LmArgs
     const long long v = vv[k];
     const int i = (int)(v % L.nx);
     const int j = (int)((v / L.nx) % L.ny);
+    const int z = (int)(v / ((long long)L.nx * L.ny));
     float gt[4], Ht;
-    huber_terms(L, V, v, i, j, tr[k], gt, Ht);
+    huber_terms(L, V, v, i, j, z, tr[k], gt, Ht);
     // Phi(trial) - Phi(current) < -TAU Phi(current)
     const float dphi = 0.5f * ((ts.rr[k].s - ns.rr[k].s) - (ts.rr[k].c - ns.rr[k].c));
     const bool accept = solved[k] && fmaf(L.beta, Ht - Hc[k], dphi) < -TAU * phi[k];
@@ -864,17 +880,24 @@ int kcs_ki(int64_t n_vox, const float* params, float* ki, void* stream) {
   return KCS_OK;
 }
 
-int kcs_huber_grad(int nx, int ny, int nz, const float* params, float delta, float* grad,
-                   void* stream) {
+int kcs_huber_grad_nb(int nx, int ny, int nz, const float* params, float delta,
+                      int neighbourhood, float* grad, void* stream) {
   clear_error();
   KCS_REQUIRE(params && grad, "NULL argument");
   KCS_REQUIRE(nx > 0 && ny > 0 && nz > 0, "sizes must be positive");
   KCS_REQUIRE(delta > 0.f, "delta must be positive");
+  KCS_REQUIRE(neighbourhood == 8 || neighbourhood == 26, "neighbourhood %d must be 8 or 26",
+              neighbourhood);
   const long long n = (long long)nx * ny * nz;
-  k_huber_grad<<<(unsigned)((n + 255) / 256), 256, 0, as_stream(stream)>>>(nx, ny, nz, params,
-                                                                            delta, grad);
+  k_huber_grad<<<(unsigned)((n + 255) / 256), 256, 0, as_stream(stream)>>>(
+      nx, ny, nz, params, delta, neighbourhood == 26 ? 1 : 0, grad);
   KCS_LAUNCHED();
   return KCS_OK;
+}
+
+int kcs_huber_grad(int nx, int ny, int nz, const float* params, float delta, float* grad,
+                   void* stream) {
+  return kcs_huber_grad_nb(nx, ny, nz, params, delta, 8, grad, stream);
 }
 
 size_t kcs_lm_workspace_size(int nx, int ny, int nz) {
@@ -887,7 +910,17 @@ int kcs_map_lm_fit_ex(const kcs_kinetics_t* k, int nx, int ny, int nz, const voi
                       int x_type, const float* x_scale, float* params, float* lambda,
                       int n_steps, float beta_h, float delta, float* F_out, void* workspace,
                       size_t ws_bytes, void* stream) {
+  return kcs_map_lm_fit_nb(k, nx, ny, nz, x, x_type, x_scale, params, lambda, n_steps, beta_h,
+                           delta, 8, F_out, workspace, ws_bytes, stream);
+}
+
+int kcs_map_lm_fit_nb(const kcs_kinetics_t* k, int nx, int ny, int nz, const void* x,
+                      int x_type, const float* x_scale, float* params, float* lambda,
+                      int n_steps, float beta_h, float delta, int neighbourhood, float* F_out,
+                      void* workspace, size_t ws_bytes, void* stream) {
   clear_error();
+  KCS_REQUIRE(neighbourhood == 8 || neighbourhood == 26, "neighbourhood %d must be 8 or 26",
+              neighbourhood);
   KCS_REQUIRE(k && x && params, "NULL argument");
   KCS_REQUIRE(nx > 0 && ny > 0 && nz > 0, "sizes must be positive");
   KCS_REQUIRE(x_type == KCS_F32 || x_type == KCS_BF16 || x_type == KCS_F16,
@@ -909,6 +942,7 @@ int kcs_map_lm_fit_ex(const kcs_kinetics_t* k, int nx, int ny, int nz, const voi
   L.lambda = lambda ? lambda : lam_ws;
   L.beta = beta_h;
   L.delta = delta;
+  L.nb3d = neighbourhood == 26 ? 1 : 0;
   const size_t smem = sizeof(float) * LM_BLOCK_VOX * (k->M + 1);
   auto kern = x_type == KCS_BF16 ? k_lm_step<__nv_bfloat16>
             : x_type == KCS_F16 ? k_lm_step<__half> : k_lm_step<float>;

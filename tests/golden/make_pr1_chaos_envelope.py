@@ -52,6 +52,16 @@ def main():
             "Ki_rel_l2": rel_l2(c[2][0][inside], a[2][0][inside]),
             "Ki_class_mean_rel": max(abs(c[2][0][lab == k].mean() / a[2][0][lab == k].mean() - 1)
                                      for k in (1, 2, 3))}
+    # the same sensitivity for the other two methods of Sec. IV-A
+    out["methods"] = {}
+    for method in ("direct", "indirect"):
+        c = OI.icm(P["g"], P["counts"], kappa, P["ts"], P["te"], S.FENG, 5, 10, 0.1, 0.1, 0.01,
+                   method=method)
+        d = OI.icm(P["g"], P["counts"], kappa * (1 + EPS), P["ts"], P["te"], S.FENG, 5, 10,
+                   0.1, 0.1, 0.01, method=method)
+        out["methods"][method] = {"image_rel_l2": rel_l2(d[0], c[0]),
+                                  "model_tac_rel_l2": rel_l2(d[3], c[3]),
+                                  "loglik_rel": abs(ll(d[0]) / ll(c[0]) - 1)}
     with open(os.path.join(HERE, "pr1_chaos_envelope.json"), "w") as f:
         json.dump(out, f, indent=1)
     print(out)

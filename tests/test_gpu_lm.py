@@ -98,3 +98,42 @@ def test_fit_writes_model_tacs(cuda_ok):
     K.map_lm_fit(kin, _t(x), pg, 3, 0.1, 0.01, F_out=Fo)
     F_ref = K.tac_eval(kin, pg)
     assert torch.equal(Fo, F_ref)
+
+
+@pytest.mark.parametrize("delta", [0.01, 1e30])
+def test_huber_grad_3d_matches_oracle(cuda_ok, delta):
+    import paper_1803_10045_b300 as K
+    rng = np.random.default_rng(9)
+    maps = rng.uniform(0, 0.1, (4, 5, 13, 11))
+    got = K.huber_grad(_t(maps), delta, neighbourhood=26).double().cpu().numpy()
+    ref = OL.huber_grad(_f32(maps), delta, nbhd="3d")
+    np.testing.assert_allclose(got, ref, atol=4e-6)
+
+
+@pytest.mark.parametrize("beta", [0.1, 50.0])
+def test_single_step_3d_neighbourhood_teacher_forced(cuda_ok, beta):
+    """The 26-neighbour (3x3x3) Huber variant: 3 planes of jittered PR1 maps."""
+    import paper_1803_10045_b300 as K
+    cases = [_lm_case(seed) for seed in (0, 1, 2)]
+    P = cases[0][0]
+    x = np.concatenate([c[1] for c in cases])
+    maps = np.concatenate([c[2] for c in cases], axis=1)
+    lam = np.concatenate([c[3] for c in cases])
+    kin = K.Kinetics(P["ts"], P["te"], S.FENG)
+    pg, lg = _t(maps), _t(lam)
+    K.map_lm_fit(kin, _t(x), pg, 1, beta, 0.01, lam=lg, neighbourhood=26)
+    got = pg.double().cpu().numpy()
+    lam_g = lg.double().cpu().numpy()
+    ref, lam_r, acc_r, _ = OL.lm_step(x, maps, lam, P["ts"], P["te"], S.FENG, beta, 0.01,
+                                      nbhd="3d")
+    acc_g = np.isclose(lam_g, np.maximum(lam / 10, 1e-7), rtol=1e-5)
+    agree = acc_g == acc_r
+    print(f"3d beta={beta}: accept agreement {agree.mean():.4f}, accepted {acc_r.mean():.3f}")
+    assert agree.mean() > 0.99
+    tol = 1e-3 * np.maximum(np.abs(ref), FLOOR[:, None, None, None])
+    both = np.broadcast_to(agree[None], ref.shape)
+    assert np.all(np.abs(got - ref)[both] <= tol[both])
+    # the 3D prior couples the planes: the result differs from the in-plane one
+    p2 = _t(maps)
+    K.map_lm_fit(kin, _t(x), p2, 1, beta, 0.01, lam=_t(lam))
+    assert not torch.equal(p2, pg)

@@ -115,3 +115,40 @@ def test_step_solves_damped_normal_equations(beta):
             np.testing.assert_allclose(new.reshape(4, -1)[:, v],
                                        np.clip(maps.reshape(4, -1)[:, v] + step, 0, [2, 2, 1, 1]),
                                        rtol=1e-10)
+
+
+def test_huber_3d_large_delta_is_26_neighbour_laplacian():
+    rng = np.random.default_rng(5)
+    m = rng.random((4, 5, 6, 7))
+    g = lm.huber_grad(m, 1e30, nbhd="3d")
+    nb = sum(np.roll(m, (-dz, -dy, -dx), axis=(1, 2, 3)) for dz, dy, dx in lm.NEIGHBOURS_3D)
+    np.testing.assert_allclose(g[:, 1:-1, 1:-1, 1:-1], (26 * m - nb)[:, 1:-1, 1:-1, 1:-1],
+                               rtol=1e-12)
+    # corner voxel (0,0,0): 7 neighbours
+    ref = 7 * m[:, 0, 0, 0] - sum(m[:, dz, dy, dx] for dz in (0, 1) for dy in (0, 1)
+                                  for dx in (0, 1) if (dz, dy, dx) != (0, 0, 0))
+    np.testing.assert_allclose(g[:, 0, 0, 0], ref, rtol=1e-12)
+
+
+def test_huber_3d_single_plane_equals_2d_and_constant_is_zero():
+    rng = np.random.default_rng(6)
+    m = rng.random((4, 1, 8, 9)) * 0.05
+    np.testing.assert_array_equal(lm.huber_grad(m, 0.01, nbhd="3d"), lm.huber_grad(m, 0.01))
+    np.testing.assert_array_equal(lm.huber_local(m, m, 0.01, nbhd="3d"), lm.huber_local(m, m, 0.01))
+    assert np.all(lm.huber_grad(np.full((4, 3, 4, 4), 0.2), 0.01, nbhd="3d") == 0.0)
+
+
+def test_huber_3d_grad_is_gradient_of_energy():
+    rng = np.random.default_rng(7)
+    maps = rng.random((4, 3, 5, 5)) * 0.05
+    d = 0.01
+
+    def energy(m):
+        return 0.5 * lm.huber_local(m, m, d, nbhd="3d").sum()
+
+    g = lm.huber_grad(maps, d, nbhd="3d")
+    for idx in [(0, 1, 2, 3), (2, 0, 0, 0), (3, 2, 4, 1)]:
+        e = np.zeros_like(maps)
+        e[idx] = 1e-7
+        fd = (energy(maps + e) - energy(maps - e)) / 2e-7
+        assert abs(fd - g[idx]) < 1e-6

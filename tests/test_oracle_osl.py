@@ -116,3 +116,24 @@ def test_stored_update_reduces_to_float64_update_at_fine_grid():
                                     randoms_k=osl.subset_slice(r, g, k)) * scale
         err = np.abs(got - ref) / ref
         assert err.max() < tol, (kind, err.max())
+
+
+def test_icm_methods_compose_as_defined():
+    """INDIRECT = OSEM passes then one fit; DIRECT = KCS with beta_h = 0."""
+    import kcs_synth as S
+    from oracle import icm, lm
+    g, xt, dt, kappa, r, counts, _ = _setup(S=3, randoms=False)
+    counts = counts[:, :, :, :]
+    ts = np.concatenate([[0.0], np.cumsum(dt)[:-1]])
+    te = np.cumsum(dt)
+    x0 = osl.initial_image(g, counts, kappa, dt, 2)
+    xi0 = np.broadcast_to(np.array(S.XI0)[:, None, None, None], (4, 2, 24, 24)).copy()
+    xa, xia, _, _ = icm.icm(g, counts, kappa, ts, te, S.FENG, 2, 2, 0.1, 0.1, 0.01,
+                            method="indirect")
+    xr = osl.osl_pass(g, osl.osl_pass(g, x0, counts, kappa, dt), counts, kappa, dt)
+    assert np.array_equal(xa, xr)
+    xir, _ = lm.lm_fit(xr, xi0, 2, ts, te, S.FENG, 0.0, 0.01)
+    assert np.array_equal(xia, xir)
+    xd, xid, _, _ = icm.icm(g, counts, kappa, ts, te, S.FENG, 2, 2, 0.1, 0.1, 0.01, method="direct")
+    xk, xik, _, _ = icm.icm(g, counts, kappa, ts, te, S.FENG, 2, 2, 0.1, 0.0, 0.01, method="kcs")
+    assert np.array_equal(xd, xk) and np.array_equal(xid, xik)
