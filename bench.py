@@ -551,10 +551,12 @@ def run_mc(args):
     ybar = K.forward_project(g, K.tac_eval(kin, truth)) * dt    # every plane the same
     for trues in [float(t) for t in args.mc_trues.split(",")]:
         for beta_kp in [float(b) for b in args.mc_beta_kp.split(",")]:
-            _mc_case(args, K, torch, W, R, g, kin, dt, ybar, xi1, paper, trues, beta_kp)
+            for beta_h in [float(b) for b in args.mc_beta_h.split(",")]:
+                _mc_case(args, K, torch, W, R, g, kin, dt, ybar, xi1, paper, trues, beta_kp,
+                         beta_h)
 
 
-def _mc_case(args, K, torch, W, R, g, kin, dt, ybar, xi1, paper, trues, beta_kp):
+def _mc_case(args, K, torch, W, R, g, kin, dt, ybar, xi1, paper, trues, beta_kp, beta_h):
     M = W.n_frames
     kappa = float(trues / ybar[0].double().sum().item())
     counts = torch.poisson(ybar * kappa, generator=torch.Generator("cuda").manual_seed(args.seed))
@@ -588,7 +590,7 @@ def _mc_case(args, K, torch, W, R, g, kin, dt, ybar, xi1, paper, trues, beta_kp)
         params = torch.empty((4, R, W.ny, W.nx), device="cuda")
         params[:] = start[:, None, None, None]
         st = K.Study(g, kin, dt, kappa, counts, x, params, n_lm=N_LM, beta_kp=beta_kp,
-                     beta_h=BETA_H, delta=DELTA, method=method)
+                     beta_h=beta_h, delta=DELTA, method=method)
         done = 0
         result[method] = {}
         for c in checkpoints:
@@ -605,9 +607,9 @@ def _mc_case(args, K, torch, W, R, g, kin, dt, ybar, xi1, paper, trues, beta_kp)
         "realisations": R, "checkpoints": checkpoints, "seed": args.seed,
         "config": {"workload": (f"{args.mc_workload}: 64x64, {M} frames, 96 bins x 90 angles, "
                                 f"4 subsets, {trues:g} trues per realisation, beta_kp "
-                                f"{beta_kp:g}, beta_h 0.1 (KCS), delta 0.01, 10 LM steps per "
-                                "iteration"),
-                   "trues": trues, "beta_kp": beta_kp,
+                                f"{beta_kp:g}, beta_h {beta_h:g} (KCS), delta 0.01, 10 LM "
+                                "steps per iteration"),
+                   "trues": trues, "beta_kp": beta_kp, "beta_h": beta_h,
                    "wall_s": round(wall, 2)},
         "results": result}))
 
@@ -637,6 +639,7 @@ def main():
     ap.add_argument("--mc-workload", choices=["pr1", "paper"], default="pr1")
     ap.add_argument("--mc-trues", default="1e6", help="comma-separated expected trues per realisation")
     ap.add_argument("--mc-beta-kp", default="0.1", help="comma-separated kinetics-prior weights")
+    ap.add_argument("--mc-beta-h", default="0.1", help="comma-separated Huber weights (KCS)")
     ap.add_argument("--seed", type=int, default=0)
     args = ap.parse_args()
     if args.mc:
