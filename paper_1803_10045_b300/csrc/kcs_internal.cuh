@@ -98,13 +98,21 @@ inline size_t align256(size_t n) { return (n + 255) & ~size_t(255); }
 // Each a-dependent channel is e^{-aD} sum_n a^n c_n with c_n >= 0.  The series
 // is tabulated around NCENT expansion centres a0 = c * DCENT (Taylor shift of the
 // float64 base series, again non-negative coefficients), so a voxel sums at most
-// 13 terms in delta = a - a0 in [0, DCENT) whatever a is.  Table layout
+// 8 terms (intervals <= 5 min, delta = a - a0 in [0, 1/16)) whatever a is; the
+// centre spacing trades table size (60 centres, 0.8 MB for 24 intervals) for
+// series length (1/4 spacing needed up to 13 terms).  Table layout
 // [interval][term][part][centre] (part = 4 channels): the lanes of a warp, each
 // on its own centre, read one short contiguous run per load.
 constexpr int NB = 128;         // base terms tabulated in float64
-constexpr int KC = 16;          // terms per centre
-constexpr int NCENT = 15;       // centres 0, 0.25, ..., 3.5 (valid for 0 <= a < 3.75)
-constexpr float DCENT = 0.25f;
+#ifndef KCS_CENT_PER_UNIT
+#define KCS_CENT_PER_UNIT 16
+#endif
+#ifndef KCS_KC
+#define KCS_KC 10
+#endif
+constexpr int KC = KCS_KC;                       // terms per centre
+constexpr int NCENT = 15 * KCS_CENT_PER_UNIT / 4;   // valid for 0 <= a < NCENT * DCENT
+constexpr float DCENT = 1.0f / KCS_CENT_PER_UNIT;
 constexpr int NCH = 12;         // channels per term, padded to 3 float4
 constexpr double DT_MAX = 5.0;  // longest propagation interval (min)
 

@@ -13,9 +13,10 @@
 // (10 channels).  A series of positive terms has no cancellation, is smooth
 // through a -> 0 and a -> any input exponent, and gives d/da in closed form.
 // The coefficients (input moments) are tabulated once per frame schedule in
-// float64 by Gauss-Legendre quadrature and re-expanded around 15 centres a0;
-// each voxel then evaluates, per interval, one exp and Horner recurrences of at
-// most 16 terms in delta = a - a0 >= 0 in float32.
+// float64 by Gauss-Legendre quadrature and re-expanded around 60 centres
+// a0 = c / 16; each voxel then evaluates, per interval, Horner recurrences of
+// at most 8 terms in delta = a - a0 >= 0 in float32 (one exp per distinct
+// interval length).
 
 #include <cmath>
 #include <algorithm>
@@ -166,7 +167,7 @@ struct Series {
 
 // Evaluates F_m (and dF_m/d(K1,k2,k3,Vb) when JAC) of VPT voxels frame by frame
 // and hands each finished frame to sink(v, m, F, J0, J1, J2, J3).  Each voxel
-// sums its series around its own centre (delta < DCENT, at most 13 terms).
+// sums its series around its own centre (delta < DCENT, at most 8 terms).
 template <int VPT, bool JAC, class Sink>
 __device__ __forceinline__ void eval_model(const KinDev& kd, const float (&K1)[VPT],
                                            const float (&k2)[VPT], const float (&k3)[VPT],
