@@ -59,18 +59,20 @@ def _series_terms(y):
     return int(np.ceil(2 * y + 5.75 * np.sqrt(y) + 3.75))
 
 
-def lm_flops_per_voxel_step(interval_lengths, a=0.19, frames=24):
-    """Nominal float32 flops (FMA = 2) of one MAP-LM voxel-step at k2 + k3 = a
-    (grey matter; centre 0, delta = a): Horner sums of the Jacobian pass (6
-    channels) and the trial pass (3 channels) over every interval, the
-    input-free channels (4 + 2) once per distinct interval length, the state
-    recursion per interval (~30 + 12 flop), per frame the model, residual and
-    normal equations (~70 flop), ~100 flop for the 4x4 solve and ~384 for the
-    Huber terms of the current and trial points."""
-    K = [_series_terms(a * D) for D in interval_lengths]
-    Kd = [_series_terms(a * D) for D in sorted(set(interval_lengths))]
-    return (9 * 2 * sum(K) + 6 * 2 * sum(Kd) + 42 * len(interval_lengths) + 70 * frames
-            + 100 + 384)
+def lm_flops_per_voxel_step(interval_lengths, frames=24, delta=1.0 / 16, n_lm=10):
+    """Nominal float32 flops (FMA = 2) of one MAP-LM voxel-step: one model +
+    Jacobian evaluation (at the trial point; the normal equations of the
+    current point are kept from the previous step) with the series lengths of
+    the widest centre offset delta (the warp's trip count): Horner sums of 6
+    channels over every interval, the input-free channels (4) once per
+    distinct interval length, ~30 flop of state recursion per interval, ~55
+    per frame (model, residual, normal equations); ~100 for the 4x4 solve and
+    ~384 for the Huber terms of the current and trial points; plus the
+    evaluation at the start point amortised over the n_lm steps of a fit."""
+    K = [_series_terms(delta * D) for D in interval_lengths]
+    Kd = [_series_terms(delta * D) for D in sorted(set(interval_lengths))]
+    pass_ = 6 * 2 * sum(K) + 4 * 2 * sum(Kd) + 30 * len(interval_lengths) + 55 * frames
+    return round(pass_ * (1 + 1 / n_lm) + 100 + 384)
 
 
 _TS, _TE = S.schedule(S.SCHEDULES["pr2"])
@@ -375,7 +377,8 @@ def run_ours(args):
     alg = {  # algorithmic bytes per launch
         "fwd_ratio": img + sino_k * (cs + es),             # read x, counts_k; write rho
         "bwd_osl": sino_k * es + 2 * img + img32,          # read rho, x, F; write x
-        "lm_step": img + 2 * 4 * V * 4 + 2 * V * 4,        # x; params in/out; lambda in/out
+        "lm_step": img + 2 * 4 * V * 4 + 2 * V * 4 + 2 * 16 * V * 4,   # x; maps, lambda and
+                                                           # normal equations in/out
         "tac_eval": 4 * V * 4 + img32,
     }
     n_launch = {"fwd_ratio": S_, "bwd_osl": S_, "lm_step": N_LM, "tac_eval": 1}

@@ -244,7 +244,7 @@ int kcs_map_lm_fit_nb(const kcs_kinetics_t* k, int nx, int ny, int nz, const voi
  * cannot allocate device memory: an application that owns all device memory
  * through its own pool and forbids raw allocations by plug-ins, or a service
  * that must not allocate after start-up.  It is kcs_map_lm_fit with the
- * workspace replaced by a fixed array inside the library (about 5 MB, held on
+ * workspace replaced by a fixed array inside the library (about 10 MB, held on
  * every GPU that loads the library until the process exits), so it takes no
  * workspace argument and never allocates.
  *  - At most KCS_LM_STATIC_MAX_VOXELS voxels (nx*ny*nz); larger problems are
@@ -256,7 +256,7 @@ int kcs_map_lm_fit_nb(const kcs_kinetics_t* k, int nx, int ny, int nz, const voi
  *    corrupt each other; serialise them.  Nothing in the array needs to start at
  *    zero (each step writes what it later reads).
  * Arguments as for kcs_map_lm_fit. */
-#define KCS_LM_STATIC_MAX_VOXELS 262144
+#define KCS_LM_STATIC_MAX_VOXELS 65536
 int kcs_map_lm_fit_static(const kcs_kinetics_t* k, int nx, int ny, int nz, const float* x,
                           float* params, float* lambda, int n_steps, float beta_h, float delta,
                           float* F_out, void* stream);

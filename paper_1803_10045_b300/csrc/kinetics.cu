@@ -471,6 +471,8 @@ struct LmArgs {
   int reset_lambda;
   float beta, delta;
   int nb3d;              // Huber neighbourhood: 0 in-plane 3x3, 1 the 3x3x3 cube
+  const float* ne_in;    // [16][V] normal equations at the current point
+  float* ne_out;         // [16][V] normal equations at the returned point
 };
 
 // Compensated (Kahan) float32 sum: the value is s - c.
@@ -507,18 +509,6 @@ struct NormalSink {
   }
 };
 
-// Sum of squared residuals at the trial point.  Both sums are compensated, so
-// their difference resolves objective changes far below the acceptance margin
-// TAU (the rounding of the individual squares is ~6e-8 of the sum), and no
-// per-frame copy of the current model TAC has to be kept.
-struct TrialSink {
-  const float* xs[LM_VPT];
-  KSum rr[LM_VPT];
-  __device__ void operator()(int v, int m, float F, float, float, float, float) {
-    const float r = xs[v][m] - F;
-    rr[v].add(r * r);
-  }
-};
 
 // Float-float arithmetic for the 4x4 solve: a value is hi + lo with |lo| at
 // most half an ulp of hi (about 48 significant bits).  Built from the
@@ -631,14 +621,34 @@ __device__ __forceinline__ void huber_terms(const LmArgs& L, long long V, long l
   }
 }
 
+// The damped normal equations of a voxel at its current point, kept between
+// steps in the workspace as 16 floats [16][V]: A00 A01 A02 A03 A11 A12 A13 A22
+// A23 A33, b0..b3 (J^T r), and the compensated sum of squared residuals (s, c).
+constexpr int NE_FIELDS = 16;
+
+__device__ __forceinline__ void store_normal(float* ne, long long V, long long v, const Normal& n,
+                                             const KSum& rr) {
+  const float f[NE_FIELDS] = {n.A00, n.A01, n.A02, n.A03, n.A11, n.A12, n.A13, n.A22,
+                              n.A23, n.A33, n.b0,  n.b1,  n.b2,  n.b3,  rr.s,  rr.c};
+#pragma unroll
+  for (int q = 0; q < NE_FIELDS; ++q) ne[q * V + v] = f[q];
+}
+
+__device__ __forceinline__ void load_normal(const float* ne, long long V, long long v, Normal& n,
+                                            KSum& rr) {
+  float f[NE_FIELDS];
+#pragma unroll
+  for (int q = 0; q < NE_FIELDS; ++q) f[q] = __ldg(ne + q * V + v);
+  n = Normal{f[0], f[1], f[2], f[3], f[4], f[5], f[6], f[7], f[8], f[9], f[10], f[11], f[12], f[13]};
+  rr = KSum{f[14], f[15]};
+}
+
+// Stage the block's TACs (stored type -> activity) in shared memory.
 template <class TX>
-__global__ void __launch_bounds__(LM_THREADS, KCS_LM_MINBLOCKS) k_lm_step(LmArgs L) {
-  extern __shared__ float xs_all[];
+__device__ __forceinline__ void stage_tacs(const LmArgs& L, float* xs_all, long long v0,
+                                           long long nv) {
   const int M = L.kd.M;
   const int ld = M + 1;
-  const long long V = (long long)L.nx * L.ny * L.nz;
-  const long long v0 = (long long)blockIdx.x * LM_BLOCK_VOX;
-  const long long nv = min((long long)LM_BLOCK_VOX, V - v0);
   const TX* xg = static_cast<const TX*>(L.x);
   for (long long e = threadIdx.x; e < nv * M; e += LM_THREADS) {
     const long long r = e / M, m = e - r * M;
@@ -646,11 +656,21 @@ __global__ void __launch_bounds__(LM_THREADS, KCS_LM_MINBLOCKS) k_lm_step(LmArgs
     xs_all[r * ld + m] = L.x_scale ? xv * __ldg(L.x_scale + m) : xv;
   }
   __syncthreads();
+}
+
+// Normal equations at the start maps p_in (before the first step).
+template <class TX>
+__global__ void __launch_bounds__(LM_THREADS, KCS_LM_MINBLOCKS) k_lm_normal(LmArgs L) {
+  extern __shared__ float xs_all[];
+  const int ld = L.kd.M + 1;
+  const long long V = (long long)L.nx * L.ny * L.nz;
+  const long long v0 = (long long)blockIdx.x * LM_BLOCK_VOX;
+  const long long nv = min((long long)LM_BLOCK_VOX, V - v0);
+  stage_tacs<TX>(L, xs_all, v0, nv);
   long long vv[LM_VPT];
   bool act[LM_VPT];
   float K1[LM_VPT], k2[LM_VPT], k3[LM_VPT], Vb[LM_VPT];
   NormalSink ns;
-  TrialSink ts;
 #pragma unroll
   for (int k = 0; k < LM_VPT; ++k) {
     const int lv = threadIdx.x + k * LM_THREADS;
@@ -661,26 +681,51 @@ __global__ void __launch_bounds__(LM_THREADS, KCS_LM_MINBLOCKS) k_lm_step(LmArgs
     k3[k] = L.p_in[2 * V + vv[k]];
     Vb[k] = L.p_in[3 * V + vv[k]];
     ns.xs[k] = xs_all + (act[k] ? lv : 0) * ld;
-    ts.xs[k] = ns.xs[k];
     ns.n[k] = Normal{0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
     ns.rr[k] = KSum{0.f, 0.f};
-    ts.rr[k] = KSum{0.f, 0.f};
   }
   eval_model<LM_VPT, true>(L.kd, K1, k2, k3, Vb, ns);
-  float tr[LM_VPT][4], phi[LM_VPT], Hc[LM_VPT], lam[LM_VPT];
+#pragma unroll
+  for (int k = 0; k < LM_VPT; ++k)
+    if (act[k]) store_normal(L.ne_out, V, vv[k], ns.n[k], ns.rr[k]);
+}
+
+// One synchronous MAP-LM step.  The normal equations at the current point come
+// from the workspace (written by the previous step or k_lm_normal); the model
+// and its Jacobian are evaluated once, at the trial point, which yields both
+// the trial objective and, if the trial is accepted, the next step's normal
+// equations.  A rejected trial keeps the current ones (only lambda changes).
+template <class TX>
+__global__ void __launch_bounds__(LM_THREADS, KCS_LM_MINBLOCKS) k_lm_step(LmArgs L) {
+  extern __shared__ float xs_all[];
+  const int ld = L.kd.M + 1;
+  const long long V = (long long)L.nx * L.ny * L.nz;
+  const long long v0 = (long long)blockIdx.x * LM_BLOCK_VOX;
+  const long long nv = min((long long)LM_BLOCK_VOX, V - v0);
+  stage_tacs<TX>(L, xs_all, v0, nv);
+  long long vv[LM_VPT];
+  bool act[LM_VPT];
+  float tr[LM_VPT][4], phi[LM_VPT], Hc[LM_VPT], lam[LM_VPT], rrs[LM_VPT], rrcmp[LM_VPT];
   bool solved[LM_VPT];
 #pragma unroll
   for (int k = 0; k < LM_VPT; ++k) {
-    const long long v = vv[k];
+    const int lv = threadIdx.x + k * LM_THREADS;
+    act[k] = lv < nv;
+    const long long v = act[k] ? v0 + lv : v0;
+    vv[k] = v;
     const int i = (int)(v % L.nx);
     const int j = (int)((v / L.nx) % L.ny);
     const int z = (int)(v / ((long long)L.nx * L.ny));
-    const float xi[4] = {K1[k], k2[k], k3[k], Vb[k]};
+    const float xi[4] = {L.p_in[v], L.p_in[V + v], L.p_in[2 * V + v], L.p_in[3 * V + v]};
+    Normal n;
+    KSum rr;
+    load_normal(L.ne_in, V, v, n, rr);
+    rrs[k] = rr.s;
+    rrcmp[k] = rr.c;
     float g[4];
     huber_terms(L, V, v, i, j, z, xi, g, Hc[k]);
-    phi[k] = fmaf(0.5f, ns.rr[k].s - ns.rr[k].c, L.beta * Hc[k]);
+    phi[k] = fmaf(0.5f, rr.s - rr.c, L.beta * Hc[k]);
     lam[k] = L.reset_lambda ? LAMBDA0 : L.lambda[v];
-    const Normal& n = ns.n[k];
     const float bq[4] = {n.b0, n.b1, n.b2, n.b3};
     ff rhs[4];
 #pragma unroll
@@ -691,13 +736,20 @@ __global__ void __launch_bounds__(LM_THREADS, KCS_LM_MINBLOCKS) k_lm_step(LmArgs
     for (int q = 0; q < 4; ++q)
       tr[k][q] = solved[k] ? fminf(fmaxf(xi[q] + step[q], c_lo[q]), c_hi[q]) : xi[q];
   }
+  NormalSink ns;
+#pragma unroll
+  for (int k = 0; k < LM_VPT; ++k) {
+    ns.xs[k] = xs_all + (act[k] ? (int)(vv[k] - v0) : 0) * ld;
+    ns.n[k] = Normal{0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+    ns.rr[k] = KSum{0.f, 0.f};
+  }
   {
     float t1[LM_VPT], t2[LM_VPT], t3[LM_VPT], t4[LM_VPT];
 #pragma unroll
     for (int k = 0; k < LM_VPT; ++k) {
       t1[k] = tr[k][0]; t2[k] = tr[k][1]; t3[k] = tr[k][2]; t4[k] = tr[k][3];
     }
-    eval_model<LM_VPT, false>(L.kd, t1, t2, t3, t4, ts);
+    eval_model<LM_VPT, true>(L.kd, t1, t2, t3, t4, ns);
   }
 #pragma unroll
   for (int k = 0; k < LM_VPT; ++k) {
@@ -709,12 +761,17 @@ __global__ void __launch_bounds__(LM_THREADS, KCS_LM_MINBLOCKS) k_lm_step(LmArgs
     float gt[4], Ht;
     huber_terms(L, V, v, i, j, z, tr[k], gt, Ht);
     // Phi(trial) - Phi(current) < -TAU Phi(current)
-    const float dphi = 0.5f * ((ts.rr[k].s - ns.rr[k].s) - (ts.rr[k].c - ns.rr[k].c));
+    const float dphi = 0.5f * ((ns.rr[k].s - rrs[k]) - (ns.rr[k].c - rrcmp[k]));
     const bool accept = solved[k] && fmaf(L.beta, Ht - Hc[k], dphi) < -TAU * phi[k];
-    const float xi[4] = {K1[k], k2[k], k3[k], Vb[k]};
 #pragma unroll
-    for (int q = 0; q < 4; ++q) L.p_out[q * V + v] = accept ? tr[k][q] : xi[q];
+    for (int q = 0; q < 4; ++q) L.p_out[q * V + v] = accept ? tr[k][q] : L.p_in[q * V + v];
     L.lambda[v] = accept ? fmaxf(lam[k] * 0.1f, LAMBDA_MIN) : fminf(lam[k] * 10.f, LAMBDA_MAX);
+    if (accept) {
+      store_normal(L.ne_out, V, v, ns.n[k], ns.rr[k]);
+    } else {
+#pragma unroll
+      for (int q = 0; q < NE_FIELDS; ++q) L.ne_out[q * V + v] = __ldg(L.ne_in + q * V + v);
+    }
   }
 }
 
@@ -904,7 +961,9 @@ int kcs_huber_grad(int nx, int ny, int nz, const float* params, float delta, flo
 size_t kcs_lm_workspace_size(int nx, int ny, int nz) {
   if (nx <= 0 || ny <= 0 || nz <= 0) return 0;
   const size_t V = (size_t)nx * ny * nz;
-  return align256(4 * V * sizeof(float)) + align256(V * sizeof(float));
+  // ping-pong maps, lambda, two copies of the per-voxel normal equations
+  return align256(4 * V * sizeof(float)) + align256(V * sizeof(float)) +
+         2 * align256(NE_FIELDS * V * sizeof(float));
 }
 
 int kcs_map_lm_fit_ex(const kcs_kinetics_t* k, int nx, int ny, int nz, const void* x,
@@ -932,9 +991,14 @@ int kcs_map_lm_fit_nb(const kcs_kinetics_t* k, int nx, int ny, int nz, const voi
               "workspace too small (%zu < %zu)", ws_bytes, kcs_lm_workspace_size(nx, ny, nz));
   cudaStream_t s = as_stream(stream);
   const long long V = (long long)nx * ny * nz;
-  float* pong = static_cast<float*>(workspace);
-  float* lam_ws = reinterpret_cast<float*>(static_cast<char*>(workspace) +
-                                           align256(4 * (size_t)V * sizeof(float)));
+  char* w = static_cast<char*>(workspace);
+  float* pong = reinterpret_cast<float*>(w);
+  w += align256(4 * (size_t)V * sizeof(float));
+  float* lam_ws = reinterpret_cast<float*>(w);
+  w += align256((size_t)V * sizeof(float));
+  float* ne_a = reinterpret_cast<float*>(w);
+  w += align256(NE_FIELDS * (size_t)V * sizeof(float));
+  float* ne_b = reinterpret_cast<float*>(w);
   LmArgs L;
   L.kd = k->dev();
   L.nx = nx; L.ny = ny; L.nz = nz;
@@ -947,21 +1011,36 @@ int kcs_map_lm_fit_nb(const kcs_kinetics_t* k, int nx, int ny, int nz, const voi
   const size_t smem = sizeof(float) * LM_BLOCK_VOX * (k->M + 1);
   auto kern = x_type == KCS_BF16 ? k_lm_step<__nv_bfloat16>
             : x_type == KCS_F16 ? k_lm_step<__half> : k_lm_step<float>;
-  KCS_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-  // Ask for the smallest shared-memory carve-out that holds KCS_LM_MINBLOCKS
-  // blocks, leaving the rest of the SM's 256 KB to L1 (coefficient rows).
-  KCS_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout,
-                                KCS_LM_CARVEOUT));
+  auto kinit = x_type == KCS_BF16 ? k_lm_normal<__nv_bfloat16>
+             : x_type == KCS_F16 ? k_lm_normal<__half> : k_lm_normal<float>;
+  for (auto f : {kern, kinit}) {
+    KCS_CUDA(cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    // Ask for the smallest shared-memory carve-out that holds KCS_LM_MINBLOCKS
+    // blocks, leaving the rest of the SM's 256 KB to L1 (coefficient rows).
+    KCS_CUDA(cudaFuncSetAttribute(f, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                  KCS_LM_CARVEOUT));
+  }
   const unsigned blocks = (unsigned)((V + LM_BLOCK_VOX - 1) / LM_BLOCK_VOX);
   float* cur = params;
   float* nxt = pong;
+  float* ne_cur = ne_a;
+  float* ne_nxt = ne_b;
+  if (n_steps > 0) {
+    L.p_in = params;
+    L.ne_out = ne_cur;
+    kinit<<<blocks, LM_THREADS, smem, s>>>(L);
+    KCS_LAUNCHED();
+  }
   for (int it = 0; it < n_steps; ++it) {
     L.p_in = cur;
     L.p_out = nxt;
+    L.ne_in = ne_cur;
+    L.ne_out = ne_nxt;
     L.reset_lambda = (it == 0 && !lambda) ? 1 : 0;
     kern<<<blocks, LM_THREADS, smem, s>>>(L);
     KCS_LAUNCHED();
     std::swap(cur, nxt);
+    std::swap(ne_cur, ne_nxt);
   }
   if (cur != params)
     KCS_CUDA(cudaMemcpyAsync(params, cur, 4 * (size_t)V * sizeof(float), cudaMemcpyDeviceToDevice, s));
@@ -984,9 +1063,10 @@ int kcs_map_lm_fit(const kcs_kinetics_t* k, int nx, int ny, int nz, const float*
 // not allocate device memory themselves.  The array lives in every GPU that
 // loads the library until the process exits.
 namespace {
-constexpr size_t kStaticLmBytes =
+constexpr size_t kStaticLmBytes =   // the layout of kcs_lm_workspace_size at the maximum size
     ((4 * (size_t)KCS_LM_STATIC_MAX_VOXELS * sizeof(float) + 255) & ~size_t(255)) +
-    (size_t)KCS_LM_STATIC_MAX_VOXELS * sizeof(float);
+    (((size_t)KCS_LM_STATIC_MAX_VOXELS * sizeof(float) + 255) & ~size_t(255)) +
+    2 * (((size_t)NE_FIELDS * KCS_LM_STATIC_MAX_VOXELS * sizeof(float) + 255) & ~size_t(255));
 static __device__ __align__(256) unsigned char g_lm_scratch[kStaticLmBytes];
 constexpr int kMaxDevices = 64;
 std::mutex g_lm_scratch_mu;

@@ -41,17 +41,23 @@ def main():
     # rounding alone moves the ICM trajectory.
     lab = S.labels_pr1()
     inside = lab > 0
+    # (the maximum over three stored runs with kappa x (1, 1 + EPS, 1 - EPS): a
+    # chaotic quantity needs more than one sample to bound)
     out["storage"] = {}
     for kind in ("bf16", "f16"):
-        c = OI.icm(P["g"], P["counts"], kappa, P["ts"], P["te"], S.FENG, 5, 10, 0.1, 0.1, 0.01,
-                   storage=kind)
-        out["storage"][kind] = {
-            "image_rel_l2": rel_l2(c[0], a[0]), "model_tac_rel_l2": rel_l2(c[3], a[3]),
-            "K1_rel_l2": rel_l2(c[1][0, 0][inside], a[1][0, 0][inside]),
-            "k3_rel_l2": rel_l2(c[1][2, 0][inside], a[1][2, 0][inside]),
-            "Ki_rel_l2": rel_l2(c[2][0][inside], a[2][0][inside]),
-            "Ki_class_mean_rel": max(abs(c[2][0][lab == k].mean() / a[2][0][lab == k].mean() - 1)
-                                     for k in (1, 2, 3))}
+        worst = {}
+        for f in (1.0, 1 + EPS, 1 - EPS):
+            c = OI.icm(P["g"], P["counts"], kappa * f, P["ts"], P["te"], S.FENG, 5, 10, 0.1, 0.1,
+                       0.01, storage=kind)
+            m = {"image_rel_l2": rel_l2(c[0], a[0]), "model_tac_rel_l2": rel_l2(c[3], a[3]),
+                 "K1_rel_l2": rel_l2(c[1][0, 0][inside], a[1][0, 0][inside]),
+                 "k3_rel_l2": rel_l2(c[1][2, 0][inside], a[1][2, 0][inside]),
+                 "Ki_rel_l2": rel_l2(c[2][0][inside], a[2][0][inside]),
+                 "Ki_class_mean_rel": float(max(
+                     abs(c[2][0][lab == k].mean() / a[2][0][lab == k].mean() - 1)
+                     for k in (1, 2, 3)))}
+            worst = {k: max(v, worst.get(k, 0.0)) for k, v in m.items()}
+        out["storage"][kind] = worst
     # the same sensitivity for the other two methods of Sec. IV-A
     out["methods"] = {}
     for method in ("direct", "indirect"):
