@@ -261,6 +261,13 @@ int kcs_map_lm_fit_static(const kcs_kinetics_t* k, int nx, int ny, int nz, const
                           float* params, float* lambda, int n_steps, float beta_h, float delta,
                           float* F_out, void* stream);
 
+/* Device-side failure detection: the number of bounded waits inside the
+ * library's kernels (bulk-copy completion barriers) that ran out instead of
+ * completing, summed over the process on the current device.  A timed-out
+ * kernel skips the rest of its work rather than hanging.  Synchronous (reads a
+ * device counter); returns KCS_ERR_TIMEOUT if the count is non-zero. */
+int kcs_device_status(unsigned int* wait_timeouts);
+
 /* --------------------------------------------------------------- ICM
  * A study binds a geometry, a kinetics table and the caller's device buffers;
  * kcs_icm_iterate runs Sec. II-D's alternation on it, all on one stream:

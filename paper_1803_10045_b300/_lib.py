@@ -86,6 +86,7 @@ SIGNATURES = {
     "kcs_study_iterations": (i32, [vp]),
     "kcs_study_set_graph": (i32, [vp, i32]),
     "kcs_study_fit": (i32, [vp, i32, vp]),
+    "kcs_device_status": (i32, [C.POINTER(C.c_uint)]),
 }
 
 for _name, (_res, _args) in SIGNATURES.items():

@@ -128,6 +128,15 @@ def _randoms(g, randoms, M):
     return _ptr(randoms, "randoms", g.sino_shape(M)), RANDOMS_FULL
 
 
+def device_status():
+    """Bounded in-kernel waits that ran out on the current device (0 = none)."""
+    n = C.c_uint(0)
+    rc = lib.kcs_device_status(C.byref(n))
+    if rc not in (0, 4):
+        check(rc)
+    return n.value
+
+
 def osl_workspace_size(g: Geometry, M):
     return lib.kcs_osl_workspace_size(g.handle, M)
 

@@ -386,6 +386,204 @@ __global__ void __launch_bounds__(BK_TILE * BK_TILE) k_back_tiled(ProjArgs p, in
   }
 }
 
+// ------------------------------------------------------------ bulk-copy staging
+// Device-side count of bounded waits that ran out (a broken invariant, never
+// expected); read by kcs_device_status.
+__device__ unsigned int g_wait_timeouts;
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count)
+               : "memory");
+}
+// Arrive on bar (count 1) announcing `bytes` of asynchronous copies.
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
+               "r"(bytes)
+               : "memory");
+}
+// One bulk copy global -> this CTA's shared memory, completion counted on bar.
+// dst, src and bytes must be multiples of 16.
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes,
+                                         uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::
+          "r"(smem_u32(dst)),
+      "l"(src), "r"(bytes), "r"(smem_u32(bar))
+      : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+      " selp.u32 %0, 1, 0, p;\n}"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+// Bounded wait for phase `parity` of bar; false (and the device counter
+// raised) if it did not complete within the limit.
+constexpr int MBAR_SPIN_LIMIT = 1 << 22;
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
+  for (int it = 0; it < MBAR_SPIN_LIMIT; ++it)
+    if (mbar_try_wait(bar, parity)) return true;
+  atomicAdd(&g_wait_timeouts, 1u);
+  return false;
+}
+
+// The tiled gather back-projection of k_back_tiled with the ratio rows of
+// each angle brought into shared memory by one bulk copy (the rows of one
+// angle and plane are contiguous in the [Z][A_k][B][M] sinogram), issued by a
+// single thread for all angles of the chunk at once; every thread waits only
+// for the angle it is about to use, so the copies of later angles overlap the
+// work on earlier ones and no thread spends issue slots on staging.  Rows are
+// dense in shared memory (pitch = one bin's frames).
+template <int MQ, int MODE, class TX, class TY>
+__global__ void __launch_bounds__(BK_TILE * BK_TILE) k_back_bulk(ProjArgs p, int rows_max,
+                                                                  int achunk) {
+  constexpr int RB = MQ * 4 * (int)sizeof(TY);   // bytes of one bin's frames
+  static_assert(RB % 16 == 0, "bulk copies move multiples of 16 bytes");
+  extern __shared__ __align__(16) unsigned char sraw[];   // [achunk][rows_max] rows
+  __shared__ int s_lo[BK_ACHUNK], s_cnt[BK_ACHUNK], s_a[BK_ACHUNK];
+  __shared__ AngleTab s_T[BK_ACHUNK];
+  __shared__ __align__(8) uint64_t s_bar[BK_ACHUNK];
+  const int ntx = (p.nx + BK_TILE - 1) / BK_TILE;
+  const int nty = (p.ny + BK_TILE - 1) / BK_TILE;
+  const int tile = blockIdx.x;
+  const int tx = tile % ntx;
+  const int ty = (tile / ntx) % nty;
+  const int z = tile / (ntx * nty);
+  const int i0 = tx * BK_TILE, j0 = ty * BK_TILE;
+  const int i1 = min(i0 + BK_TILE, p.nx) - 1, j1 = min(j0 + BK_TILE, p.ny) - 1;
+  const int i = i0 + (threadIdx.x % BK_TILE);
+  const int j = j0 + (threadIdx.x / BK_TILE);
+  const bool valid = i < p.nx && j < p.ny;
+  const float bc = 0.5f * (float)(p.B - 1);
+  if (threadIdx.x == 0) {
+    for (int c = 0; c < BK_ACHUNK; ++c) mbar_init(&s_bar[c], 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  float4 acc[MQ];
+#pragma unroll
+  for (int q = 0; q < MQ; ++q) acc[q] = f4(0.f);
+  float sens = 0.f;
+  bool ok = true;
+  uint32_t parity = 0;
+  for (int a0 = 0; a0 < p.n_sub; a0 += achunk, parity ^= 1u) {
+    const int na = min(achunk, p.n_sub - a0);
+    if ((int)threadIdx.x < na) {
+      // union of the candidate ranges of the tile's four corners
+      const int a = p.sub[a0 + threadIdx.x];
+      const AngleTab T = p.ang[a];
+      s_a[threadIdx.x] = a;
+      s_T[threadIdx.x] = T;
+      const int n_major = T.xmajor ? p.nx : p.ny;
+      const int n_minor = T.xmajor ? p.ny : p.nx;
+      const float tc = 0.5f * (float)(n_major - 1);
+      const float centre = 0.5f * (float)(n_minor - 1);
+      const int ta = T.xmajor ? i0 : j0, tb = T.xmajor ? i1 : j1;
+      const int ma = T.xmajor ? j0 : i0, mb = T.xmajor ? j1 : i1;
+      int lo = p.B, hi = -1;
+      for (int c = 0; c < 4; ++c) {
+        const int t = (c & 1) ? tb : ta;
+        const int m = (c & 2) ? mb : ma;
+        int l, h;
+        bin_range(T, m, inner_pos((float)t - tc, T.gamma, centre), bc, p.B, l, h);
+        lo = min(lo, l);
+        hi = max(hi, h);
+      }
+      lo = max(0, lo - 1);
+      hi = min(p.B - 1, hi + 1);
+      s_lo[threadIdx.x] = lo;
+      s_cnt[threadIdx.x] = max(0, min(hi - lo + 1, rows_max));
+    }
+    // the previous chunk's rows have been read by every thread (generic proxy)
+    // before the copies below (async proxy) overwrite them
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      for (int c = 0; c < na; ++c) {
+        const uint32_t bytes = (uint32_t)s_cnt[c] * RB;
+        mbar_expect_tx(&s_bar[c], bytes);
+        if (bytes) {
+          const char* src = static_cast<const char*>(p.y) +
+                            ((size_t)(z * p.n_sub + a0 + c) * p.B + s_lo[c]) * RB;
+          bulk_g2s(sraw + (size_t)c * rows_max * RB, src, bytes, &s_bar[c]);
+        }
+      }
+    }
+    for (int c = 0; c < na; ++c) {
+      ok = mbar_wait(&s_bar[c], parity) && ok;
+      if (!valid || !ok) continue;
+      const int a = s_a[c];
+      const AngleTab T = s_T[c];
+      const int n_major = T.xmajor ? p.nx : p.ny;
+      const int n_minor = T.xmajor ? p.ny : p.nx;
+      const int t = T.xmajor ? i : j;
+      const int m = T.xmajor ? j : i;
+      const float tc = 0.5f * (float)(n_major - 1);
+      const float centre = 0.5f * (float)(n_minor - 1);
+      const float inner = inner_pos((float)t - tc, T.gamma, centre);
+      int b_lo, b_hi;
+      bin_range_tight(T, m, inner, bc, p.B, b_lo, b_hi);
+      const int lo = s_lo[c];
+      b_lo = max(b_lo, lo);
+      b_hi = min(b_hi, lo + s_cnt[c] - 1);
+      const TY* rows = reinterpret_cast<const TY*>(sraw + (size_t)c * rows_max * RB);
+      const size_t binrow = (size_t)(z * p.A + a) * p.B;
+      for (int b = b_lo; b <= b_hi; ++b) {
+        const float fr = minor_pos((float)b - bc, T.beta, inner);
+        const float fl = floorf(fr);
+        const int jj = (int)fl;
+        const float f = fr - fl;
+        float wt = (jj == m) ? 1.0f - f : ((jj + 1 == m) ? f : 0.0f);
+        if (wt == 0.0f) continue;
+        wt *= T.w;
+        if (MODE == 1 && p.bin_factor) wt *= __ldg(p.bin_factor + binrow + b);
+        const TY* row = rows + (size_t)(b - lo) * MQ * 4;
+#pragma unroll
+        for (int q = 0; q < MQ; ++q) fma4(acc[q], wt, ld4(row + q * 4));
+        sens += wt;
+      }
+    }
+    __syncthreads();
+  }
+  if (!valid || !ok) return;
+  const size_t vi = ((size_t)(z * p.ny + j) * p.nx + i) * MQ;
+  if (MODE == 0) {
+#pragma unroll
+    for (int q = 0; q < MQ; ++q) st4(static_cast<TX*>(p.xout) + (vi + q) * 4, acc[q]);
+    return;
+  }
+  if (!(sens > 0.f)) return;   // x unchanged where no ray of the subset sees the voxel
+  const float ks = p.kappa * sens;
+#pragma unroll
+  for (int q = 0; q < MQ; ++q) {
+    float4 xv = ld4(static_cast<const TX*>(p.x) + (vi + q) * 4);
+    const float4 sc = p.xscale ? __ldg(p.xscale + q) : f4(1.f);
+    if (p.xscale) xv = mul4(xv, sc);            // stored image -> activity
+    const float4 dt = __ldg(p.dt + q);
+    float4 den = make_float4(dt.x * ks, dt.y * ks, dt.z * ks, dt.w * ks);
+    if (p.F) {
+      const float4 Fv = __ldg(p.F + vi + q);
+      const float ps = p.prior_scale;
+      den.x = fmaxf(fmaf(ps, xv.x - Fv.x, den.x), 1e-3f * den.x);
+      den.y = fmaxf(fmaf(ps, xv.y - Fv.y, den.y), 1e-3f * den.y);
+      den.z = fmaxf(fmaf(ps, xv.z - Fv.z, den.z), 1e-3f * den.z);
+      den.w = fmaxf(fmaf(ps, xv.w - Fv.w, den.w), 1e-3f * den.w);
+    }
+    xv.x = xv.x * (p.kappa * dt.x * acc[q].x) / den.x;
+    xv.y = xv.y * (p.kappa * dt.y * acc[q].y) / den.y;
+    xv.z = xv.z * (p.kappa * dt.z * acc[q].z) / den.z;
+    xv.w = xv.w * (p.kappa * dt.w * acc[q].w) / den.w;
+    if (p.xscale) xv = make_float4(xv.x / sc.x, xv.y / sc.y, xv.z / sc.z, xv.w / sc.w);
+    st4(static_cast<TX*>(p.xout) + (vi + q) * 4, xv);
+  }
+}
+
 // Sensitivity sum_{d in S_k} n_d p_vd: the same gather with unit data.
 __global__ void __launch_bounds__(256) k_sens(ProjArgs p, float* sens_out) {
   const long long vox = (long long)blockIdx.x * blockDim.x + threadIdx.x;
@@ -544,8 +742,25 @@ static int back_rows_max(const kcs_geometry* g) {
 
 constexpr size_t BK_SMEM_MAX = 200 * 1024;   // dynamic shared memory budget per block
 
+#ifndef KCS_BACK_BULK
+#define KCS_BACK_BULK 1
+#endif
+
 template <int MQ, int MODE, class TX, class TY>
 static int launch_back_mq(const ProjArgs& p, int rows_max, cudaStream_t s) {
+  if constexpr (KCS_BACK_BULK && (MQ * 4 * sizeof(TY)) % 16 == 0) {
+    const size_t row_bytes = (size_t)MQ * 4 * sizeof(TY) * rows_max;
+    const int achunk = (int)std::min<size_t>(BK_ACHUNK, BK_SMEM_MAX / row_bytes);
+    KCS_REQUIRE(achunk >= 1, "bins are too fine relative to voxels for the tiled back-projection");
+    const size_t smem = row_bytes * achunk;
+    KCS_CUDA(cudaFuncSetAttribute(k_back_bulk<MQ, MODE, TX, TY>,
+                                  cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    const long long tiles = (long long)((p.nx + BK_TILE - 1) / BK_TILE) *
+                            ((p.ny + BK_TILE - 1) / BK_TILE) * p.nz;
+    k_back_bulk<MQ, MODE, TX, TY><<<(unsigned)tiles, BK_TILE * BK_TILE, smem, s>>>(p, rows_max,
+                                                                                 achunk);
+    return KCS_OK;
+  }
   const size_t row_bytes = sizeof(float4) * rows_max * bk_pitch(MQ);
   const int achunk = (int)std::min<size_t>(BK_ACHUNK, BK_SMEM_MAX / row_bytes);
   KCS_REQUIRE(achunk >= 1, "bins are too fine relative to voxels for the tiled back-projection");
@@ -929,6 +1144,13 @@ int kcs_init_image_ex(const kcs_geometry_t* g, int n_frames, const float* frame_
     k_broadcast_frames<<<nb, 256, 0, s>>>(static_cast<float*>(x), n_vox, M, cval, x_scale);
   KCS_LAUNCHED();
   return KCS_OK;
+}
+
+int kcs_device_status(unsigned int* wait_timeouts) {
+  clear_error();
+  KCS_REQUIRE(wait_timeouts, "NULL argument");
+  KCS_CUDA(cudaMemcpyFromSymbol(wait_timeouts, g_wait_timeouts, sizeof(unsigned int)));
+  return *wait_timeouts ? KCS_ERR_TIMEOUT : KCS_OK;
 }
 
 int kcs_init_image(const kcs_geometry_t* g, int n_frames, const float* frame_dt, float kappa,
