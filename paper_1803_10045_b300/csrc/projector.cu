@@ -549,6 +549,11 @@ __global__ void __launch_bounds__(BK_TILE * BK_TILE) k_back_bulk(ProjArgs p, int
         sens += wt;
       }
     }
+    if (!ok) {
+      // a wait ran out: before this CTA's shared memory can be reused, wait
+      // once more (bounded) for every copy of the chunk still in flight
+      for (int c = 0; c < na; ++c) mbar_wait(&s_bar[c], parity);
+    }
     __syncthreads();
   }
   if (!valid || !ok) return;
