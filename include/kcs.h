@@ -267,6 +267,13 @@ int kcs_map_lm_fit_static(const kcs_kinetics_t* k, int nx, int ny, int nz, const
  * kernel skips the rest of its work rather than hanging.  Synchronous (reads a
  * device counter); returns KCS_ERR_TIMEOUT if the count is non-zero. */
 int kcs_device_status(unsigned int* wait_timeouts);
+/* Reset that counter to zero (synchronous). */
+int kcs_device_status_reset(void);
+/* Self-test of the failure path: one kernel waits, with at most spin_limit
+ * polls (1 .. 2^20), on a barrier that nothing completes, so the wait runs
+ * out and the counter read by kcs_device_status rises by one.  No fault, no
+ * hang; the context stays usable. */
+int kcs_selftest_wait_timeout(int spin_limit, void* stream);
 
 /* --------------------------------------------------------------- ICM
  * A study binds a geometry, a kinetics table and the caller's device buffers;
@@ -333,6 +340,10 @@ int kcs_study_set_graph(kcs_study_t* st, int enable);
 int kcs_study_fit(kcs_study_t* st, int n_steps, void* stream);
 /* Number of ICM iterations issued so far on this study. */
 int kcs_study_iterations(const kcs_study_t* st);
+/* Set that number, e.g. when resuming from a checkpoint of x, params and F:
+ * the next iteration then builds its prior from F as the interrupted run
+ * would have. */
+int kcs_study_set_iterations(kcs_study_t* st, int iterations);
 
 #ifdef __cplusplus
 }

@@ -84,9 +84,12 @@ SIGNATURES = {
     "kcs_destroy_study": (i32, [vp]),
     "kcs_icm_iterate": (i32, [vp, i32, vp]),
     "kcs_study_iterations": (i32, [vp]),
+    "kcs_study_set_iterations": (i32, [vp, i32]),
     "kcs_study_set_graph": (i32, [vp, i32]),
     "kcs_study_fit": (i32, [vp, i32, vp]),
     "kcs_device_status": (i32, [C.POINTER(C.c_uint)]),
+    "kcs_device_status_reset": (i32, []),
+    "kcs_selftest_wait_timeout": (i32, [i32, vp]),
 }
 
 for _name, (_res, _args) in SIGNATURES.items():

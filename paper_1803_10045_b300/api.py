@@ -372,6 +372,36 @@ class Study:
     def iterations(self):
         return lib.kcs_study_iterations(self.handle)
 
+    def save(self, path):
+        """Checkpoint the ICM state (image series, kinetic maps, model TACs,
+        iteration count) to an .npz file; arrays keep their storage dtype's
+        bits.  Synchronises the current stream."""
+        import numpy as np
+        torch.cuda.current_stream().synchronize()
+
+        def host(t):
+            if t.dtype in (torch.bfloat16, torch.float16):
+                return t.view(torch.int16).cpu().numpy(), str(t.dtype)
+            return t.cpu().numpy(), str(t.dtype)
+        x, xd = host(self.x)
+        np.savez(path, x=x, x_dtype=xd, params=self.params.cpu().numpy(),
+                 F=self.F.cpu().numpy(), iterations=self.iterations)
+
+    def restore(self, path):
+        """Load a checkpoint written by save into this study's buffers (same
+        shapes and storage types) and resume its iteration count."""
+        import numpy as np
+        d = np.load(path)
+        if str(d["x_dtype"]) != str(self.x.dtype):
+            raise ValueError(f"checkpoint holds {d['x_dtype']}, study x is {self.x.dtype}")
+        x = torch.from_numpy(d["x"])
+        if self.x.dtype in (torch.bfloat16, torch.float16):
+            x = x.view(self.x.dtype)
+        self.x.copy_(x)
+        self.params.copy_(torch.from_numpy(d["params"]))
+        self.F.copy_(torch.from_numpy(d["F"]))
+        check(lib.kcs_study_set_iterations(self.handle, int(d["iterations"])))
+
     def close(self):
         if getattr(self, "handle", None):
             lib.kcs_destroy_study(self.handle)

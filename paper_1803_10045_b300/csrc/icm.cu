@@ -8,6 +8,8 @@
 
 #include <algorithm>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "kcs_internal.cuh"
 
 struct kcs_study {
@@ -34,18 +36,27 @@ int issue_iteration(const kcs_study* st, bool prior, void* stream) {
   const kcs_geometry* g = d.geom;
   const bool indirect = d.method == KCS_METHOD_INDIRECT;
   if (indirect) prior = false;
+  // host-side ranges (visible in Nsight timelines) around the issue of each phase
+  nvtxRangePushA("kcs::osl_pass");
   for (int k = 0; k < g->S; ++k) {
     const int rc = kcs_osl_update_ex(g, k, d.n_frames, d.frame_dt, d.kappa, d.counts,
                                      d.counts_type, d.randoms, d.randoms_layout, d.bin_factor,
                                      prior ? d.F : nullptr, prior ? d.beta_kp : 0.f,
                                      d.sigma2 > 0.f ? d.sigma2 : 1.f, d.x, d.x_type, d.x_scale,
                                      d.workspace, d.ws_bytes, stream);
-    if (rc) return rc;
+    if (rc) {
+      nvtxRangePop();
+      return rc;
+    }
   }
+  nvtxRangePop();
   if (indirect) return KCS_OK;
-  return kcs_map_lm_fit_nb(d.kin, g->nx, g->ny, g->nz, d.x, d.x_type, d.x_scale, d.params,
+  nvtxRangePushA("kcs::map_lm_fit");
+  const int rc = kcs_map_lm_fit_nb(d.kin, g->nx, g->ny, g->nz, d.x, d.x_type, d.x_scale, d.params,
                            nullptr, d.n_lm, fit_beta_h(d), d.delta, fit_nbhd(d), d.F, d.workspace,
                            d.ws_bytes, stream);
+  nvtxRangePop();
+  return rc;
 }
 
 // Record the steady-state iteration once into a CUDA graph.  Capture runs on a
@@ -131,6 +142,14 @@ int kcs_study_set_graph(kcs_study_t* st, int enable) {
 }
 
 int kcs_study_iterations(const kcs_study_t* st) { return st ? st->iterations : -1; }
+
+int kcs_study_set_iterations(kcs_study_t* st, int iterations) {
+  clear_error();
+  KCS_REQUIRE(st, "study is NULL");
+  KCS_REQUIRE(iterations >= 0, "iterations < 0");
+  st->iterations = iterations;
+  return KCS_OK;
+}
 
 int kcs_study_fit(kcs_study_t* st, int n_steps, void* stream) {
   clear_error();

@@ -434,6 +434,20 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
   return false;
 }
 
+// Failure-detection self-test: a barrier nothing arrives on, waited for with a
+// small limit; the wait runs out and raises the counter like a real timeout.
+__global__ void k_selftest_wait(int limit) {
+  __shared__ __align__(8) uint64_t bar;
+  if (threadIdx.x == 0) {
+    mbar_init(&bar, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncthreads();
+  bool done = false;
+  for (int it = 0; it < limit && !done; ++it) done = mbar_try_wait(&bar, 0);
+  if (!done && threadIdx.x == 0) atomicAdd(&g_wait_timeouts, 1u);
+}
+
 // The tiled gather back-projection of k_back_tiled with the ratio rows of
 // each angle brought into shared memory by one bulk copy (the rows of one
 // angle and plane are contiguous in the [Z][A_k][B][M] sinogram), issued by a
@@ -1147,6 +1161,21 @@ int kcs_init_image_ex(const kcs_geometry_t* g, int n_frames, const float* frame_
     k_broadcast_frames<<<nb, 256, 0, s>>>(static_cast<__half*>(x), n_vox, M, cval, x_scale);
   else
     k_broadcast_frames<<<nb, 256, 0, s>>>(static_cast<float*>(x), n_vox, M, cval, x_scale);
+  KCS_LAUNCHED();
+  return KCS_OK;
+}
+
+int kcs_device_status_reset(void) {
+  clear_error();
+  const unsigned int zero = 0;
+  KCS_CUDA(cudaMemcpyToSymbol(g_wait_timeouts, &zero, sizeof zero));
+  return KCS_OK;
+}
+
+int kcs_selftest_wait_timeout(int spin_limit, void* stream) {
+  clear_error();
+  KCS_REQUIRE(spin_limit > 0 && spin_limit <= (1 << 20), "spin_limit must be in (0, 2^20]");
+  k_selftest_wait<<<1, 32, 0, as_stream(stream)>>>(spin_limit);
   KCS_LAUNCHED();
   return KCS_OK;
 }
