@@ -568,7 +568,7 @@ __global__ void __launch_bounds__(BK_TILE * BK_TILE) k_back_bulk(ProjArgs p, int
       // once more (bounded) for every copy of the chunk still in flight
       for (int c = 0; c < na; ++c) mbar_wait(&s_bar[c], parity);
     }
-    __syncthreads();
+    if (a0 + achunk < p.n_sub) __syncthreads();   // rows are reused by the next chunk
   }
   if (!valid || !ok) return;
   const size_t vi = ((size_t)(z * p.ny + j) * p.nx + i) * MQ;
