@@ -480,6 +480,7 @@ __global__ void __launch_bounds__(BK_TILE * BK_TILE) k_back_bulk(ProjArgs p, int
     for (int c = 0; c < BK_ACHUNK; ++c) mbar_init(&s_bar[c], 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
+  __syncthreads();   // barriers initialised before anyone waits on them
   float4 acc[MQ];
 #pragma unroll
   for (int q = 0; q < MQ; ++q) acc[q] = f4(0.f);
@@ -488,44 +489,50 @@ __global__ void __launch_bounds__(BK_TILE * BK_TILE) k_back_bulk(ProjArgs p, int
   uint32_t parity = 0;
   for (int a0 = 0; a0 < p.n_sub; a0 += achunk, parity ^= 1u) {
     const int na = min(achunk, p.n_sub - a0);
-    if ((int)threadIdx.x < na) {
-      // union of the candidate ranges of the tile's four corners
-      const int a = p.sub[a0 + threadIdx.x];
-      const AngleTab T = p.ang[a];
-      s_a[threadIdx.x] = a;
-      s_T[threadIdx.x] = T;
-      const int n_major = T.xmajor ? p.nx : p.ny;
-      const int n_minor = T.xmajor ? p.ny : p.nx;
-      const float tc = 0.5f * (float)(n_major - 1);
-      const float centre = 0.5f * (float)(n_minor - 1);
-      const int ta = T.xmajor ? i0 : j0, tb = T.xmajor ? i1 : j1;
-      const int ma = T.xmajor ? j0 : i0, mb = T.xmajor ? j1 : i1;
-      int lo = p.B, hi = -1;
-      for (int c = 0; c < 4; ++c) {
-        const int t = (c & 1) ? tb : ta;
-        const int m = (c & 2) ? mb : ma;
-        int l, h;
-        bin_range(T, m, inner_pos((float)t - tc, T.gamma, centre), bc, p.B, l, h);
-        lo = min(lo, l);
-        hi = max(hi, h);
+    // Warp 0 sets the chunk up while the other warps go straight to waiting on
+    // the per-angle barriers: the angle tables it writes become visible to them
+    // through the release of the barrier arrive (after a warp barrier) and the
+    // acquire of their wait.
+    if (threadIdx.x < 32) {
+      if ((int)threadIdx.x < na) {
+        // union of the candidate ranges of the tile's four corners
+        const int a = p.sub[a0 + threadIdx.x];
+        const AngleTab T = p.ang[a];
+        s_a[threadIdx.x] = a;
+        s_T[threadIdx.x] = T;
+        const int n_major = T.xmajor ? p.nx : p.ny;
+        const int n_minor = T.xmajor ? p.ny : p.nx;
+        const float tc = 0.5f * (float)(n_major - 1);
+        const float centre = 0.5f * (float)(n_minor - 1);
+        const int ta = T.xmajor ? i0 : j0, tb = T.xmajor ? i1 : j1;
+        const int ma = T.xmajor ? j0 : i0, mb = T.xmajor ? j1 : i1;
+        int lo = p.B, hi = -1;
+        for (int c = 0; c < 4; ++c) {
+          const int t = (c & 1) ? tb : ta;
+          const int m = (c & 2) ? mb : ma;
+          int l, h;
+          bin_range(T, m, inner_pos((float)t - tc, T.gamma, centre), bc, p.B, l, h);
+          lo = min(lo, l);
+          hi = max(hi, h);
+        }
+        lo = max(0, lo - 1);
+        hi = min(p.B - 1, hi + 1);
+        s_lo[threadIdx.x] = lo;
+        s_cnt[threadIdx.x] = max(0, min(hi - lo + 1, rows_max));
       }
-      lo = max(0, lo - 1);
-      hi = min(p.B - 1, hi + 1);
-      s_lo[threadIdx.x] = lo;
-      s_cnt[threadIdx.x] = max(0, min(hi - lo + 1, rows_max));
-    }
-    // the previous chunk's rows have been read by every thread (generic proxy)
-    // before the copies below (async proxy) overwrite them
-    __syncthreads();
-    if (threadIdx.x == 0) {
-      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-      for (int c = 0; c < na; ++c) {
-        const uint32_t bytes = (uint32_t)s_cnt[c] * RB;
-        mbar_expect_tx(&s_bar[c], bytes);
-        if (bytes) {
-          const char* src = static_cast<const char*>(p.y) +
-                            ((size_t)(z * p.n_sub + a0 + c) * p.B + s_lo[c]) * RB;
-          bulk_g2s(sraw + (size_t)c * rows_max * RB, src, bytes, &s_bar[c]);
+      __syncwarp();
+      if (threadIdx.x == 0) {
+        // the previous chunk's rows were read by every thread (generic proxy;
+        // block barrier at the end of that chunk) before these async copies
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        for (int c = 0; c < na; ++c) {
+          const uint32_t bytes = (uint32_t)s_cnt[c] * RB;
+          mbar_expect_tx(&s_bar[c], bytes);
+          if (bytes) {
+            const char* src = static_cast<const char*>(p.y) +
+                              ((size_t)(z * p.n_sub + a0 + c) * p.B + s_lo[c]) * RB;
+            bulk_g2s(sraw + (size_t)c * rows_max * RB, src, bytes, &s_bar[c]);
+          }
         }
       }
     }
