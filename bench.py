@@ -84,9 +84,9 @@ LM_FLOPS_PER_VOXEL_STEP = lm_flops_per_voxel_step(list(_TE - _TS), frames=len(_T
 # planes: every kernel touches each plane's data independently), valid while
 # the kernel's source file is unchanged (sha256 prefix); see profiles/.
 TRAFFIC = {
-    "lm_step": {"bytes": 247.35e6 * 127 / 16, "src": "kinetics.cu", "sha": "d7ce4d016a7eaac9"},
-    "bwd_osl": {"bytes": 505.97e6 * 127 / 16, "src": "projector.cu", "sha": "a749aa18841896d1"},
-    "fwd_ratio": {"bytes": 259.76e6 * 127 / 16, "src": "projector.cu", "sha": "a749aa18841896d1"},
+    "lm_step": {"bytes": 469.39e6 * 127 / 16, "src": "kinetics.cu", "sha": "19be0745b272f8ce"},
+    "bwd_osl": {"bytes": 506.51e6 * 127 / 16, "src": "projector.cu", "sha": "0512c95270c997be"},
+    "fwd_ratio": {"bytes": 258.78e6 * 127 / 16, "src": "projector.cu", "sha": "0512c95270c997be"},
 }
 
 
