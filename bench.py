@@ -424,7 +424,7 @@ def run_ours(args):
         "kernels": kernels,
         "voxel_lm_fits_per_s": round(V / (N_LM * lm_ms * 1e-3), 1),
         "voxel_lm_steps_per_s": round(V / (lm_ms * 1e-3), 1),
-        "gpu_launches": args.steps * (2 * S_ + N_LM + 1),
+        "gpu_launches": args.steps * (2 * S_ + N_LM + 2),   # + the start-point normal equations
         "clocks": clocks,
         "e2e": {"value": round(world * args.steps / (e2e_ms / 1e3), 4), "unit": "iter/s",
                 "h2d_bytes_per_step": counts.numel() * counts.element_size(),

@@ -82,3 +82,61 @@ def test_sharded_icm_equals_unsharded(tmp_path):
     for z0, z1, xs, xis in parts:
         np.testing.assert_allclose(xs, x[z0:z1], rtol=1e-11, atol=0)
         np.testing.assert_allclose(xis, xi[:, z0:z1], rtol=1e-9, atol=1e-14)
+
+
+def _lm_problem():
+    from oracle import kinetics as OK
+    nx, nz = 12, 5
+    ts, te = S.schedule([(2, 60), (2, 300)])
+    rng = np.random.default_rng(3)
+    xi = np.moveaxis(np.clip(S.CLASS_XI["gm"] * rng.uniform(0.5, 1.5, (nz, nx, nx, 4)), 0, None),
+                     -1, 0)
+    x = OK.model_maps(xi, ts, te, S.FENG) * (1 + 0.05 * rng.standard_normal((nz, nx, nx, 4)))
+    start = np.clip(xi * rng.uniform(0.8, 1.2, xi.shape), 0, None)
+    return x, start, ts, te
+
+
+def _lm_worker(rank, world, port, out):
+    import torch
+    from oracle import lm as OL
+    from paper_1803_10045_b300.sharding import halo_exchange
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port))
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    x, start, ts, te = _lm_problem()
+    z0, z1 = plane_shard(x.shape[0], rank, world)
+    maps = start[:, z0:z1].copy()
+    lam = np.full(maps.shape[1:], OL.LAMBDA0)
+    # the TAC halo is exchanged once (it does not change during the fit)
+    xp, xl, xh = halo_exchange(torch.from_numpy(np.moveaxis(x[z0:z1], -1, 0).copy()), rank, world)
+    xp = np.moveaxis(xp.numpy(), 0, -1)
+    for _ in range(3):
+        mp_, lo, hi = halo_exchange(torch.from_numpy(maps), rank, world)
+        lam_p = np.pad(lam, ((lo, hi), (0, 0), (0, 0)), constant_values=OL.LAMBDA0)
+        new, lam_new, _, _ = OL.lm_step(xp, mp_.numpy(), lam_p, ts, te, S.FENG, 0.5, 0.01,
+                                        nbhd="3d")
+        sl = slice(lo, lo + (z1 - z0))
+        maps, lam = new[:, sl].copy(), lam_new[sl].copy()
+    parts = [None] * world
+    dist.all_gather_object(parts, (z0, z1, maps))
+    if rank == 0:
+        np.save(out, np.array(parts, dtype=object), allow_pickle=True)
+    dist.barrier()
+    dist.destroy_process_group()
+
+
+def test_sharded_3d_prior_lm_with_halo_equals_unsharded(tmp_path):
+    """With the 26-neighbour prior the planes couple; a one-plane halo of the 4
+    maps exchanged per LM step makes the sharded fit equal the unsharded one."""
+    from oracle import lm as OL
+    out = str(tmp_path / "lm_parts.npy")
+    mp.start_processes(_lm_worker, args=(2, _free_port(), out), nprocs=2, join=True,
+                       start_method="spawn")
+    parts = np.load(out, allow_pickle=True)
+    x, start, ts, te = _lm_problem()
+    ref, _ = OL.lm_fit(x, start, 3, ts, te, S.FENG, 0.5, 0.01, nbhd="3d")
+    got = np.concatenate([p[2] for p in sorted(parts, key=lambda p: p[0])], axis=1)
+    np.testing.assert_allclose(got, ref, rtol=1e-12, atol=1e-15)
+    # and without the halo the result would differ (the exchange matters)
+    alone = np.concatenate([OL.lm_fit(x[a:b], start[:, a:b], 3, ts, te, S.FENG, 0.5, 0.01,
+                                      nbhd="3d")[0] for a, b in ((0, 3), (3, 5))], axis=1)
+    assert not np.allclose(alone, ref, rtol=1e-9)
