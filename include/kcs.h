@@ -161,6 +161,18 @@ int kcs_init_image(const kcs_geometry_t* g, int n_frames, const float* frame_dt,
                    const float* counts, const float* randoms, int randoms_layout,
                    const float* bin_factor, float* x, void* workspace, size_t ws_bytes,
                    void* stream);
+/* Poisson log-likelihood of image x against the counts over all angles, bins
+ * and frames (Eq. 1's data term; log s! dropped):
+ *   L = sum_{d,m} s_dm log ybar_dm - ybar_dm,  ybar = kappa dt_m n_d (P x) + r
+ * (s log ybar taken as 0 where ybar <= 0), accumulated in float64 into *out
+ * (device double).  A monitoring metric: one full forward projection.  Storage
+ * types as in the precision form; workspace >= 8 KB (e.g. the OSL workspace).
+ * The float64 partial sums are added atomically, so the last bits may differ
+ * between runs. */
+int kcs_loglik(const kcs_geometry_t* g, int n_frames, const float* frame_dt, float kappa,
+               const void* counts, int counts_type, const float* randoms, int randoms_layout,
+               const float* bin_factor, const void* x, int x_type, const float* x_scale,
+               double* out, void* workspace, size_t ws_bytes, void* stream);
 /* The per-frame levels c_m of that start image into level [M] (device float),
  * without writing an image: the natural per-frame scale of the precision form
  * (the start image is then stored as exactly 1). */

@@ -11,6 +11,6 @@ from ._lib import LIB_PATH, KcsError, lib  # noqa: F401
 from .api import (  # noqa: F401
     RANDOMS_FULL, RANDOMS_NONE, RANDOMS_PER_FRAME, Geometry, Kinetics, Study, back_project,
     device_status,
-    forward_project, huber_grad, init_image, init_level, ki, lm_workspace_size, map_lm_fit, osl_backproject,
+    forward_project, huber_grad, init_image, init_level, ki, loglik, lm_workspace_size, map_lm_fit, osl_backproject,
     osl_ratio, osl_update, osl_workspace_size, sensitivity, tac_eval)
 from .autograd import KineticForward, forward_model, tac_vjp  # noqa: F401,E402

@@ -63,6 +63,7 @@ SIGNATURES = {
     "kcs_osl_backproject_ex": (i32, [vp, i32, i32, vp, f32, vp, vp, vp, f32, f32, vp, i32, vp, vp]),
     "kcs_osl_update_ex": (i32, [vp, i32, i32, vp, f32, vp, i32, vp, i32, vp, vp, f32, f32, vp, i32,
                                 vp, vp, sz, vp]),
+    "kcs_loglik": (i32, [vp, i32, vp, f32, vp, i32, vp, i32, vp, vp, i32, vp, vp, vp, sz, vp]),
     "kcs_init_level": (i32, [vp, i32, vp, f32, vp, i32, vp, i32, vp, vp, vp, sz, vp]),
     "kcs_init_image_ex": (i32, [vp, i32, vp, f32, vp, i32, vp, i32, vp, vp, i32, vp, vp, sz, vp]),
     "kcs_huber_grad_nb": (i32, [i32, i32, i32, vp, f32, i32, vp, vp]),

@@ -198,6 +198,28 @@ def osl_backproject(g: Geometry, subset, x, frame_dt, kappa, rho, bin_factor=Non
     return x
 
 
+def loglik(g: Geometry, x, frame_dt, kappa, counts, randoms=None, bin_factor=None,
+           x_scale=None, workspace=None):
+    """Poisson log-likelihood sum s log ybar - ybar of image x (a 0-d float64
+    CUDA tensor; one full forward projection)."""
+    M = x.shape[-1]
+    pr, layout = _randoms(g, randoms, M)
+    xt = _storage(x, (F32, BF16, F16), "x")
+    ct = _storage(counts, (F32, U16), "counts")
+    out = torch.empty((), device=x.device, dtype=torch.float64)
+    if workspace is None:
+        workspace = _workspace(8192, x.device)
+    check(lib.kcs_loglik(
+        g.handle, M, _ptr(frame_dt, "frame_dt", (M,)), float(kappa),
+        _ptr(counts, "counts", g.sino_shape(M), dtype=counts.dtype), ct, pr, layout,
+        _ptr(bin_factor, "bin_factor", (g.nz, g.n_angles, g.n_bins), allow_none=True),
+        _ptr(x, "x", g.image_shape(M), dtype=x.dtype), xt,
+        _ptr(x_scale, "x_scale", (M,), allow_none=True),
+        C.c_void_p(out.data_ptr()), C.c_void_p(workspace.data_ptr()), workspace.numel(),
+        _stream()))
+    return out
+
+
 def init_level(g: Geometry, frame_dt, kappa, counts, randoms=None, bin_factor=None,
                workspace=None, out=None):
     """Per-frame level c_m [M] of the uniform start image (the precision form's
@@ -331,6 +353,7 @@ class Study:
         self._keep = (geom, kin, frame_dt, counts, x, params, F, randoms, bin_factor, workspace,
                       x_scale)
         self.geom, self.kin, self.x, self.params, self.F = geom, kin, x, params, F
+        self.kappa = float(kappa)
         d = StudyDesc()
         d.geom, d.kin, d.n_frames, d.kappa = geom.handle, kin.handle, M, float(kappa)
         d.frame_dt = _ptr(frame_dt, "frame_dt", (M,))
@@ -363,6 +386,12 @@ class Study:
 
     def iterate(self, n_iter=1):
         check(lib.kcs_icm_iterate(self.handle, int(n_iter), _stream()))
+
+    def loglik(self):
+        """Poisson log-likelihood of the current image (0-d float64 tensor)."""
+        g, kin, frame_dt, counts, x, params, F, randoms, bin_factor, workspace, x_scale = self._keep
+        return loglik(g, x, frame_dt, self.kappa, counts, randoms, bin_factor, x_scale,
+                      workspace)
 
     def fit(self, n_steps):
         """Post-reconstruction kinetic fit of the current image (INDIRECT)."""

@@ -121,7 +121,10 @@ struct ProjArgs {
   float kappa;
   const float4* F;          // model TACs or null
   float prior_scale;        // beta / (S sigma2)
+  double* ll_partial;       // non-null: accumulate the log-likelihood, no ratio
 };
+
+constexpr int LL_PARTS = 1024;   // partial sums of the log-likelihood
 
 // Forward projection of every frame of rays (z, ak, b); RATIO replaces the
 // projection by rho = s / (kappa dt n_d (P x) + r).
@@ -210,11 +213,34 @@ __global__ void __launch_bounds__(256) k_forward(ProjArgs p) {
   yb.y = fmaf(kn * dt.y, acc.y, r.y);
   yb.z = fmaf(kn * dt.z, acc.z, r.z);
   yb.w = fmaf(kn * dt.w, acc.w, r.w);
+  if (p.ll_partial) {
+    // Poisson log-likelihood terms s log ybar - ybar of this lane's 4 frames
+    // (log s! dropped; s log ybar taken as 0 where ybar <= 0)
+    const float t = (yb.x > 0.f ? s.x * logf(yb.x) : 0.f) - yb.x +
+                    (yb.y > 0.f ? s.y * logf(yb.y) : 0.f) - yb.y +
+                    (yb.z > 0.f ? s.z * logf(yb.z) : 0.f) - yb.z +
+                    (yb.w > 0.f ? s.w * logf(yb.w) : 0.f) - yb.w;
+    atomicAdd(p.ll_partial + (blockIdx.x & (LL_PARTS - 1)), (double)t);
+    return;
+  }
   rho.x = yb.x > 0.f ? s.x / yb.x : 0.f;
   rho.y = yb.y > 0.f ? s.y / yb.y : 0.f;
   rho.z = yb.z > 0.f ? s.z / yb.z : 0.f;
   rho.w = yb.w > 0.f ? s.w / yb.w : 0.f;
   st4(static_cast<TY*>(p.yout) + oi * 4, rho);
+}
+
+__global__ void k_sum_parts(const double* parts, int n, double* out) {
+  __shared__ double sh[256];
+  double acc = 0.0;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) acc += parts[i];
+  sh[threadIdx.x] = acc;
+  __syncthreads();
+  for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+    if ((int)threadIdx.x < w) sh[threadIdx.x] += sh[threadIdx.x + w];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) *out = sh[0];
 }
 
 // Bins whose sample at this major step can land in [m-1, m+1): the real-valued
@@ -1009,6 +1035,45 @@ int kcs_osl_ratio_ex(const kcs_geometry_t* g, int subset, int n_frames, const fl
   p.dt = reinterpret_cast<const float4*>(frame_dt);
   p.kappa = kappa;
   launch_ratio(n_frames / 4, x_type, counts_type, p, as_stream(stream));
+  KCS_LAUNCHED();
+  return KCS_OK;
+}
+
+int kcs_loglik(const kcs_geometry_t* g, int n_frames, const float* frame_dt, float kappa,
+               const void* counts, int counts_type, const float* randoms, int randoms_layout,
+               const float* bin_factor, const void* x, int x_type, const float* x_scale,
+               double* out, void* workspace, size_t ws_bytes, void* stream) {
+  clear_error();
+  int st = check_geom(g, -1, n_frames);
+  if (st) return st;
+  KCS_REQUIRE(frame_dt && counts && x && out, "frame_dt, counts, x and out must be device pointers");
+  KCS_REQUIRE(storage_ok(x_type), "x_type %d must be KCS_F32, KCS_BF16 or KCS_F16", x_type);
+  KCS_REQUIRE(counts_type == KCS_F32 || counts_type == KCS_U16, "counts_type %d must be KCS_F32 or KCS_U16",
+              counts_type);
+  KCS_REQUIRE(randoms_layout >= KCS_RANDOMS_NONE && randoms_layout <= KCS_RANDOMS_FULL,
+              "bad randoms_layout %d", randoms_layout);
+  KCS_REQUIRE(randoms_layout == KCS_RANDOMS_NONE || randoms, "randoms pointer is NULL");
+  KCS_REQUIRE(kappa > 0.f, "kappa must be positive");
+  KCS_REQUIRE(workspace && ws_bytes >= sizeof(double) * LL_PARTS, "workspace too small");
+  KCS_REQUIRE(aligned_for(x, x_type) &&
+              aligned_for(counts, counts_type == KCS_U16 ? KCS_BF16 : KCS_F32) && aligned16(frame_dt) &&
+              aligned16(randoms) && aligned16(x_scale), "arrays misaligned (16 B for float, 8 B for 16-bit)");
+  cudaStream_t s = as_stream(stream);
+  double* parts = static_cast<double*>(workspace);
+  KCS_CUDA(cudaMemsetAsync(parts, 0, sizeof(double) * LL_PARTS, s));
+  ProjArgs p = base_args(g, -1);
+  p.x = x;
+  p.xscale = reinterpret_cast<const float4*>(x_scale);
+  p.counts = counts;
+  p.randoms = reinterpret_cast<const float4*>(randoms);
+  p.randoms_layout = randoms_layout;
+  p.bin_factor = bin_factor;
+  p.dt = reinterpret_cast<const float4*>(frame_dt);
+  p.kappa = kappa;
+  p.ll_partial = parts;
+  launch_ratio(n_frames / 4, x_type, counts_type, p, s);
+  KCS_LAUNCHED();
+  k_sum_parts<<<1, 256, 0, s>>>(parts, LL_PARTS, out);
   KCS_LAUNCHED();
   return KCS_OK;
 }

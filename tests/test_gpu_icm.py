@@ -72,11 +72,17 @@ def test_pr1_icm_end_to_end(cuda_ok):
     params = _t(np.broadcast_to(np.array(S.XI0)[:, None, None, None], (4, 1, W.ny, W.nx)))
     st = K.Study(kg, kin, _t(dt), kappa, counts, x, params, n_lm=10, beta_kp=0.1, beta_h=0.1,
                  delta=0.01)
-    st.iterate(5)
+    lls = []
+    for _ in range(5):
+        st.iterate(1)
+        lls.append(st.loglik().item())
     torch.cuda.synchronize()
     assert st.iterations == 5
+    print("PR1 ICM log-likelihood per iteration:", " ".join(f"{v:.6e}" for v in lls))
     xr, xir, kir, Fr = OI.icm(P["g"], P["counts"], kappa, P["ts"], P["te"], S.FENG, 5, 10,
                               0.1, 0.1, 0.01)
+    assert abs(lls[-1] / OO.loglik(P["g"], x.double().cpu().numpy(), P["counts"], kappa, dt)
+               - 1) < 1e-5
     xg = x.double().cpu().numpy()
     xi_g = params.double().cpu().numpy()
     e_img = rel_l2(xg, xr)

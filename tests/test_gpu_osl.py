@@ -93,3 +93,29 @@ def test_pr1_osem_pass_matches_oracle(cuda_ok):
         K.osl_update(kg, k, xg, dtt, P["kappa"], ct)
         x = OO.osl_update(P["g"], x, k, P["counts"][:, P["g"].subsets[k]], P["kappa"], dt)
     assert rel_l2(xg.cpu().numpy(), x) < 1e-4
+
+
+@pytest.mark.parametrize("randoms", [False, True])
+def test_loglik_matches_oracle(cuda_ok, randoms):
+    """Poisson log-likelihood of an image (full forward projection, float64
+    accumulation) against the oracle's."""
+    import paper_1803_10045_b300 as K
+    from cases import pr1_problem
+    from oracle import osl as OO
+    P = pr1_problem()
+    W = P["W"]
+    kg = K.Geometry(W.nx, W.ny, W.nz, W.vox_mm, W.n_bins, W.n_angles, W.bin_mm, W.n_subsets)
+    dt = np.asarray(P["dt"], np.float32).astype(np.float64)
+    kappa = float(np.float32(P["kappa"]))
+    x = np.asarray(OO.osl_pass(P["g"], OO.initial_image(P["g"], P["counts"], kappa, dt, 1),
+                               P["counts"], kappa, dt), np.float32).astype(np.float64)
+    r = None
+    if randoms:
+        r_m = np.asarray(0.2 * P["counts"].mean(axis=(0, 1, 2)), np.float32).astype(np.float64)
+        r = np.broadcast_to(r_m, P["counts"].shape)
+    ref = OO.loglik(P["g"], x, P["counts"], kappa, dt, randoms=r)
+    tt = lambda a: torch.tensor(np.ascontiguousarray(a), dtype=torch.float32, device="cuda")
+    got = K.loglik(kg, tt(x), tt(dt), kappa, tt(P["counts"]),
+                   randoms=None if r is None else tt(r_m)).item()
+    print(f"loglik gpu {got:.9e} oracle {ref:.9e} rel {abs(got / ref - 1):.2e}")
+    assert abs(got / ref - 1) < 1e-5
