@@ -529,6 +529,55 @@ def run_serve(args):
         "clocks": clocks}))
 
 
+# ------------------------------------------------------------------ differentiation (PR4)
+def run_autograd(args):
+    """Config PR4: forward y = P F(theta) and its backward (exact transpose +
+    analytic kinetic Jacobian transposed) for theta [8][4][64][128][128],
+    128 bins x 96 angles, 16 frames; reports passes per second."""
+    import torch
+
+    import paper_1803_10045_b300 as K
+    torch.cuda.set_device(0)
+    nb, nx, nz, B, A = 8, 128, 64, 128, 96
+    ts, te = S.schedule(S.SCHEDULES["m16"])
+    g = K.Geometry(nx, nx, nb * nz, 2.0 * 344 / nx, B, A, 2.0 * 344 / B, 1)
+    kin = K.Kinetics(ts, te, S.FENG)
+    gen = torch.Generator("cuda").manual_seed(0)
+    base = torch.tensor(S.CLASS_XI["gm"], device="cuda")[None, :, None, None, None]
+    theta = (base * (0.5 + torch.rand((nb, 4, nz, nx, nx), device="cuda", generator=gen)))
+    theta.requires_grad_(True)
+    w = torch.rand((nb, nz, A, B, 16), device="cuda", generator=gen)
+
+    def step():
+        theta.grad = None
+        y = K.forward_model(theta, g, kin)
+        (y * w).sum().backward()
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    e = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+    fwd_ms, tot_ms = 0.0, 0.0
+    for _ in range(args.steps):
+        theta.grad = None
+        e[0].record()
+        y = K.forward_model(theta, g, kin)
+        e[1].record()
+        (y * w).sum().backward()
+        e[2].record()
+        torch.cuda.synchronize()
+        fwd_ms += e[0].elapsed_time(e[1])
+        tot_ms += e[0].elapsed_time(e[2])
+    n = args.steps
+    print(json.dumps({
+        "metric": "forward+backward passes/s (PR4 differentiable model)",
+        "value": round(1e3 * n / tot_ms, 3), "unit": "passes/s", "n_gpus": 1,
+        "higher_is_better": True, "ms_forward": round(fwd_ms / n, 3),
+        "ms_forward_backward": round(tot_ms / n, 3), "dtype": "f32", "data": "synthetic",
+        "config": {"workload": "PR4: theta [8][4][64][128][128], TAC [8][64][128][128][16], "
+                               "y [8][64][96][128][16], 128 bins x 96 angles, 16 frames",
+                   "note": "the timed backward includes torch's (y * w).sum() and its gradient"}}))
+
+
 # ------------------------------------------------------------------ MC bias/variance
 def run_mc(args):
     """Bias and variance of the kinetic maps over many noise realisations of
@@ -635,6 +684,8 @@ def main():
     ap.add_argument("--max-active", type=int, default=16)
     ap.add_argument("--serve-iters", type=int, default=10)
     ap.add_argument("--policy", choices=["fifo", "backfill"], default="fifo")
+    ap.add_argument("--autograd", action="store_true",
+                    help="config PR4: time the differentiable forward model and its backward")
     ap.add_argument("--mc", action="store_true",
                     help="bias/variance of INDIRECT, DIRECT and KCS over PR1 noise realisations")
     ap.add_argument("--realisations", type=int, default=100)
@@ -645,7 +696,9 @@ def main():
     ap.add_argument("--mc-beta-h", default="0.1", help="comma-separated Huber weights (KCS)")
     ap.add_argument("--seed", type=int, default=0)
     args = ap.parse_args()
-    if args.mc:
+    if args.autograd:
+        run_autograd(args)
+    elif args.mc:
         run_mc(args)
     elif args.serve:
         run_serve(args)

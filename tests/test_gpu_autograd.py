@@ -63,9 +63,15 @@ def test_gradient_matches_oracle(cuda_ok):
     assert rel_l2(y.detach().double().cpu().numpy(), og.forward(Fo)) < 1e-5
 
 
-def test_central_differences_on_256_voxels(cuda_ok):
+# sizes: batch, image side, planes, bins, angles; "pr4" is the full config PR4
+# (theta [8][4][64][128][128], 128 bins x 96 angles, 16 frames)
+SIZES = {"small": (2, 32, 4, 45, 24), "pr4": (8, 128, 64, 128, 96)}
+
+
+@pytest.mark.parametrize("size", ["small", "pr4"])
+def test_central_differences_on_256_voxels(cuda_ok, size):
     import paper_1803_10045_b300 as K
-    nb, nx, nz, B, A = 2, 32, 4, 45, 24
+    nb, nx, nz, B, A = SIZES[size]
     ts, te = S.schedule(S.SCHEDULES[SCHED])
     kg = K.Geometry(nx, nx, nb * nz, 2.0, B, A, 2.0, 1)
     kin = K.Kinetics(ts, te, S.FENG)
@@ -95,9 +101,10 @@ def test_central_differences_on_256_voxels(cuda_ok):
     assert np.median(errs) < 1e-3 and np.max(errs) < 3e-2, (np.median(errs), np.max(errs))
 
 
-def test_gradient_map_lowers_objective(cuda_ok):
+@pytest.mark.parametrize("size", ["small", "pr4"])
+def test_gradient_map_lowers_objective(cuda_ok, size):
     import paper_1803_10045_b300 as K
-    nb, nx, nz, B, A = 2, 32, 4, 45, 24
+    nb, nx, nz, B, A = SIZES[size]
     ts, te = S.schedule(S.SCHEDULES[SCHED])
     kg = K.Geometry(nx, nx, nb * nz, 2.0, B, A, 2.0, 1)
     kin = K.Kinetics(ts, te, S.FENG)
