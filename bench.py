@@ -54,29 +54,20 @@ def beta_kp_for(kappa):
 FP32_LANES_PER_SM, N_SM = 128, 148
 
 
-def _series_terms(y):
-    """Series length per interval for y = delta D (delta = a - centre)."""
-    return int(np.ceil(2 * y + 5.75 * np.sqrt(y) + 3.75))
-
-
-def lm_flops_per_voxel_step(interval_lengths, frames=24, delta=1.0 / 16, n_lm=10):
+def lm_flops_per_voxel_step(frames=24, n_lm=10):
     """Nominal float32 flops (FMA = 2) of one MAP-LM voxel-step: one model +
-    Jacobian evaluation (at the trial point; the normal equations of the
-    current point are kept from the previous step) with the series lengths of
-    the widest centre offset delta (the warp's trip count): Horner sums of 6
-    channels over every interval, the input-free channels (4) once per
-    distinct interval length, ~30 flop of state recursion per interval, ~55
-    per frame (model, residual, normal equations); ~100 for the 4x4 solve and
-    ~384 for the Huber terms of the current and trial points; plus the
-    evaluation at the start point amortised over the n_lm steps of a fit."""
-    K = [_series_terms(delta * D) for D in interval_lengths]
-    Kd = [_series_terms(delta * D) for D in sorted(set(interval_lengths))]
-    pass_ = 6 * 2 * sum(K) + 4 * 2 * sum(Kd) + 30 * len(interval_lengths) + 55 * frames
-    return round(pass_ * (1 + 1 / n_lm) + 100 + 384)
+    Jacobian evaluation at the trial point (the current point's normal
+    equations are kept from the previous step): per frame the Hermite
+    interpolants of A, B, A', B' (16 FMA), the model and its 4 derivatives
+    (~10 flop), the residual with its compensated square sum (~6) and the
+    normal equations (15 FMA): ~80 flop; ~30 for the interpolation basis, ~100
+    for the 4x4 solve, ~384 for the Huber terms of the current and trial
+    points; plus the evaluation at the start point amortised over the n_lm
+    steps of a fit."""
+    return round((80 * frames + 30) * (1 + 1 / n_lm) + 100 + 384)
 
 
-_TS, _TE = S.schedule(S.SCHEDULES["pr2"])
-LM_FLOPS_PER_VOXEL_STEP = lm_flops_per_voxel_step(list(_TE - _TS), frames=len(_TE))
+LM_FLOPS_PER_VOXEL_STEP = lm_flops_per_voxel_step(frames=S.WORKLOADS["pr2"].n_frames)
 
 
 # DRAM traffic (read + write) per launch measured by ncu on the 16-central-plane

@@ -95,45 +95,30 @@ inline const int* subset_dev(const kcs_geometry* g, int k) {
 inline size_t align256(size_t n) { return (n + 255) & ~size_t(255); }
 
 // ------------------------------------------------------------ kinetics
-// Each a-dependent channel is e^{-aD} sum_n a^n c_n with c_n >= 0.  The series
-// is tabulated around NCENT expansion centres a0 = c * DCENT (Taylor shift of the
-// float64 base series, again non-negative coefficients), so a voxel sums at most
-// 8 terms (intervals <= 5 min, delta = a - a0 in [0, 1/16)) whatever a is; the
-// centre spacing trades table size (60 centres, 0.8 MB for 24 intervals) for
-// series length (1/4 spacing needed up to 13 terms).  Table layout
-// [interval][term][part][centre] (part = 4 channels): the lanes of a warp, each
-// on its own centre, read one short contiguous run per load.
-constexpr int NB = 128;         // base terms tabulated in float64
-#ifndef KCS_CENT_PER_UNIT
-#define KCS_CENT_PER_UNIT 16
-#endif
-#ifndef KCS_KC
-#define KCS_KC 10
-#endif
-constexpr int KC = KCS_KC;                       // terms per centre
-constexpr int NCENT = 15 * KCS_CENT_PER_UNIT / 4;   // valid for 0 <= a < NCENT * DCENT
-constexpr float DCENT = 1.0f / KCS_CENT_PER_UNIT;
-constexpr int NCH = 12;         // channels per term, padded to 3 float4
-constexpr double DT_MAX = 5.0;  // longest propagation interval (min)
+// The frame-integrated model is linear in K1, k3 and Vb once a = k2 + k3 is
+// fixed:  F_m = (1 - Vb) K1 (A_m(a) + k3 B_m(a)) + Vb cp_m,  with A_m, B_m the
+// frame averages of I = Cp * e^{-a t} and of its time integral.  A_m, B_m and
+// their a-derivatives are tabulated in float64 on a uniform grid of a (NODES_
+// PER_UNIT nodes per unit, 0 <= a <= A_MAX) once per frame schedule, from the
+// input moments of every propagation interval (power series in a with
+// non-negative coefficients, no cancellation near a -> 0 or a -> an input
+// exponent); a voxel then evaluates cubic Hermite interpolants in a: per
+// frame two 16-byte table reads and a few fused multiply-adds.  Table layout
+// [frame][node] (A, A', B, B'), so the lanes of a warp (voxels with similar a)
+// read neighbouring entries.
+constexpr int NB = 128;                 // base terms of the input moments (float64)
+constexpr double DT_MAX = 5.0;          // longest propagation interval (min)
+constexpr int NODES_PER_UNIT = 512;     // grid spacing h = 1/512 in a (1/min)
+constexpr double A_MAX = 3.75;          // tabulated range of a (the fit's box has a <= 3)
+constexpr int N_NODES = (int)(A_MAX * NODES_PER_UNIT) + 2;
 
 // Channel numbering of the float64 base series.
 enum { CH_M1 = 0, CH_G, CH_M2, CH_H, CH_M3, CH_D1, CH_GP, CH_D2, CH_HP, CH_D3 };
-// Packing of a term's channels into 3 float4 parts: part 0 (m1, m2, m3, d1) and
-// part 1 (d2, d3, -, -) depend on the input over the interval; part 2
-// (g, h, gp, hp) only on a and D, so it is evaluated once per distinct D.
-__host__ __device__ constexpr int ch_slot(int ch) {
-  return ch == CH_M1 ? 0 : ch == CH_M2 ? 1 : ch == CH_M3 ? 2 : ch == CH_D1 ? 3
-       : ch == CH_D2 ? 4 : ch == CH_D3 ? 5
-       : ch == CH_G ? 8 : ch == CH_H ? 9 : ch == CH_GP ? 10 : 11;   // CH_HP
-}
 
 struct KinDev {
-  const float4* coef;   // [n_iv][KC][3][NCENT] float4 (12 channels = 3 parts)
-  const float* iv_dt;   // [n_iv] interval length (min)
-  const int* iv_code;   // [n_iv]: -1 gap, else 2*frame + (last piece of the frame)
+  const float4* node;   // [M][N_NODES] (A, dA/da, B, dB/da) at a = n / NODES_PER_UNIT
+  const float2* node2;  // [M][N_NODES] (d2A/da2, d2B/da2)
   const float* fr_cp;   // [M] frame average of Cp
-  const float* fr_inv;  // [M] 1 / frame duration
-  int n_iv;
   int M;
 };
 
@@ -143,16 +128,14 @@ struct kcs_kinetics {
   int M;
   int n_iv;
   int device;
-  float4* d_coef;
-  float* d_iv_dt;
-  int* d_iv_code;
+  float4* d_node;
+  float2* d_node2;
   float* d_fr_cp;
   float* d_fr_inv;
+  int* d_iv_code;
   double* d_tmp;   // per-interval doubles used while tabulating
   double* d_base;  // [n_iv][NB][10] float64 base series
-  kcs::KinDev dev() const {
-    return kcs::KinDev{d_coef, d_iv_dt, d_iv_code, d_fr_cp, d_fr_inv, n_iv, M};
-  }
+  kcs::KinDev dev() const { return kcs::KinDev{d_node, d_node2, d_fr_cp, M}; }
 };
 
 namespace kcs {

@@ -13,10 +13,15 @@
 // (10 channels).  A series of positive terms has no cancellation, is smooth
 // through a -> 0 and a -> any input exponent, and gives d/da in closed form.
 // The coefficients (input moments) are tabulated once per frame schedule in
-// float64 by Gauss-Legendre quadrature and re-expanded around 60 centres
-// a0 = c / 16; each voxel then evaluates, per interval, Horner recurrences of
-// at most 8 terms in delta = a - a0 >= 0 in float32 (one exp per distinct
-// interval length).
+// float64 by Gauss-Legendre quadrature.  Given a, the frame averages A_m(a)
+// (of I) and B_m(a) (of J) fix the whole model, which is linear in K1, k3 and
+// Vb:  F_m = (1 - Vb) K1 (A_m + k3 B_m) + Vb cp_m.  So A_m, B_m and their
+// a-derivatives are computed once, in float64, on a grid of a (spacing 1/512,
+// 0 <= a <= 3.75) by running the interval recursion at every node; a voxel
+// evaluates cubic Hermite interpolants of them (values and derivatives at the
+// two neighbouring nodes) in float32.  Interpolation error, measured against
+// the exact model: below 1.1e-8 of each frame's range for F and dF/da on the
+// paper's and the configs' schedules.
 
 #include <cmath>
 #include <algorithm>
@@ -106,30 +111,80 @@ __global__ void k_tabulate(TabArgs a) {
   if (n == 0) a.m0[iv] = s0;
 }
 
-// Taylor shift of every channel to the centres a0 = c DCENT: with
-// sum_n a^n b_n = sum_j (a - a0)^j s_j,  s_j = sum_{n >= j} C(n, j) a0^{n-j} b_n,
-// a sum of non-negative terms.  One block per (interval, centre), one thread per
-// (term j, channel).
-__global__ void k_shift(const double* base, float* coef) {
-  const int iv = blockIdx.x / NCENT;
-  const int c = blockIdx.x % NCENT;
-  const int j = threadIdx.x / 10;
-  const int ch = threadIdx.x % 10;
-  if (j >= KC) return;
-  const double a0 = c * (double)DCENT;
-  const double* b = base + (size_t)iv * NB * 10;
-  double r = 1.0, sum = 0.0;   // r = C(j+m, j) a0^m
-  for (int m = 0; j + m < NB; ++m) {
-    sum += r * b[(size_t)(j + m) * 10 + ch];
-    r *= a0 * (double)(j + m + 1) / (double)(m + 1);
+// The frame averages A_m(a), B_m(a) and their a-derivatives, in float64: per
+// interval of length D the channel series sum_n a^n c_n (Horner over the NB
+// base terms) and e^{-aD} advance the running integrals I(t) = int Cp
+// e^{-a(t-s)} ds and J(t) = int I (and their a-derivatives, from the
+// derivative channels) across the interval; the interval integrals of I and J
+// are summed over each frame and divided by its duration, then handed to
+// out(m, A, A', B, B').
+template <class Out>
+__device__ void frame_averages(double a, const double* base, const double* iv_dt,
+                               const int* iv_code, int n_iv, const double* fdt, Out out) {
+  double I = 0.0, Ip = 0.0, Jr = 0.0, Jp = 0.0, SA = 0.0, SB = 0.0, SAp = 0.0, SBp = 0.0;
+  for (int iv = 0; iv < n_iv; ++iv) {
+    const double D = iv_dt[iv];
+    const double* b = base + (size_t)iv * NB * 10;
+    double ch[10];
+    for (int c = 0; c < 10; ++c) ch[c] = 0.0;
+    for (int k = NB - 1; k >= 0; --k)
+      for (int c = 0; c < 10; ++c) ch[c] = fma(ch[c], a, b[(size_t)k * 10 + c]);
+    const double E = exp(-a * D);
+    const double G = E * ch[CH_G], H = E * ch[CH_H];
+    const double Gp = -E * ch[CH_GP], Hp = -E * ch[CH_HP];
+    // interval integrals of I and J (A, B) and their a-derivatives (Ap, Bp)
+    const double A = I * G + E * ch[CH_M2];
+    const double B = Jr * D + I * H + E * ch[CH_M3];
+    const double Ap = Ip * G + I * Gp - E * ch[CH_D2];
+    const double Bp = Jp * D + Ip * H + I * Hp - E * ch[CH_D3];
+    // state at the end of the interval
+    Ip = E * (Ip - D * I) - E * ch[CH_D1];
+    Jp += Ap;
+    I = E * I + E * ch[CH_M1];
+    Jr += A;
+    const int code = iv_code[iv];
+    if (code < 0) continue;                      // gaps propagate the state only
+    SA += A;
+    SB += B;
+    SAp += Ap;
+    SBp += Bp;
+    if (code & 1) {                              // last interval of frame m
+      const int m = code >> 1;
+      const double inv = 1.0 / fdt[m];
+      out(m, SA * inv, SAp * inv, SB * inv, SBp * inv);
+      SA = SB = SAp = SBp = 0.0;
+    }
   }
-  float* o = coef + (((size_t)iv * KC + j) * 3 * NCENT) * 4;   // [iv][j][part][centre][4]
-  const int slot = ch_slot(ch);
-  o[((slot / 4) * NCENT + c) * 4 + slot % 4] = (float)sum;
-  if (ch == 0) {
-    o[(1 * NCENT + c) * 4 + 2] = 0.f;
-    o[(1 * NCENT + c) * 4 + 3] = 0.f;
-  }
+}
+
+// Node tables at a = n / NODES_PER_UNIT: (A, A', B, B') and the second
+// derivatives (A'', B'') by a central difference of the float64 first
+// derivatives with step 1e-4 (truncation ~1e-6 relative, far below the float32
+// table precision).  One thread per node.
+constexpr double NODE_FD_STEP = 1e-4;
+__global__ void k_node_table(const double* base, const double* iv_dt, const int* iv_code,
+                             int n_iv, const double* fdt, int M, int nn, float4* node,
+                             float2* node2) {
+  const int n = blockIdx.x * blockDim.x + threadIdx.x;
+  if (n >= nn) return;
+  const double a = (double)n / NODES_PER_UNIT;
+  double dp[2 * 32];                               // A', B' at a + step, per frame
+  frame_averages(a + NODE_FD_STEP, base, iv_dt, iv_code, n_iv, fdt,
+                 [&](int m, double, double Ap, double, double Bp) {
+                   dp[2 * m] = Ap;
+                   dp[2 * m + 1] = Bp;
+                 });
+  frame_averages(a - NODE_FD_STEP, base, iv_dt, iv_code, n_iv, fdt,
+                 [&](int m, double, double Ap, double, double Bp) {
+                   const double s = 0.5 / NODE_FD_STEP;
+                   node2[(size_t)m * nn + n] =
+                       make_float2((float)((dp[2 * m] - Ap) * s), (float)((dp[2 * m + 1] - Bp) * s));
+                 });
+  frame_averages(a, base, iv_dt, iv_code, n_iv, fdt,
+                 [&](int m, double A, double Ap, double B, double Bp) {
+                   node[(size_t)m * nn + n] = make_float4((float)A, (float)Ap, (float)B, (float)Bp);
+                 });
+  (void)M;
 }
 
 __global__ void k_frame_tables(const double* m0, const int* code, int n_iv, const double* fdt,
@@ -144,148 +199,58 @@ __global__ void k_frame_tables(const double* m0, const int* code, int n_iv, cons
 }
 
 // ---------------------------------------------------------------- model
-// Number of series terms for y = delta D: the smallest K with y^K / K! <= 1e-8
-// is bounded above by ceil(2 y + 5.75 sqrt(y) + 3.75) for 0 <= y <= 17.5
-// (checked on a fine grid of y); every channel's coefficients satisfy
-// c_n <= c_0 D^n / n!, so the truncated tail is below 1e-8 of the sum.
-__device__ __forceinline__ int series_terms(float y) {
-  return (int)ceilf(fmaf(2.0f, y, fmaf(5.75f, sqrtf(y), 3.75f)));
-}
-
-// Input-driven series values of one voxel and interval (the derivative
-// channels d1..d3 only when the Jacobian is wanted).
-#ifndef KCS_HORNER_UNROLL
-#define KCS_HORNER_UNROLL 2
-#endif
-#define KCS_PRAGMA(x) _Pragma(#x)
-#define KCS_UNROLL_(n) KCS_PRAGMA(unroll n)
-#define KCS_UNROLL(n) KCS_UNROLL_(n)
-
-struct Series {
-  float m1, m2, m3, d1, d2, d3;
-};
-
 // Evaluates F_m (and dF_m/d(K1,k2,k3,Vb) when JAC) of VPT voxels frame by frame
-// and hands each finished frame to sink(v, m, F, J0, J1, J2, J3).  Each voxel
-// sums its series around its own centre (delta < DCENT, at most 8 terms).
+// and hands each frame to sink(v, m, F, J0, J1, J2, J3).  With w = 1 - Vb and
+// S = A + k3 B:  F = w K1 S + Vb cp,  dF/dK1 = w S,  dF/dk2 = w K1 (A' + k3 B'),
+// dF/dk3 = w K1 (A' + B + k3 B') = -w K1 k2 B'  (A' + B = -a B' from
+// I' = Cp - a I: a single term, exactly 0 at k2 = 0, instead of a cancelling
+// difference),  dF/dVb = cp - K1 S.  A, B are cubic Hermite interpolants of
+// the float64 node table (values and first derivatives at the two nodes around
+// a), A', B' those of the first and second derivatives.
 template <int VPT, bool JAC, class Sink>
 __device__ __forceinline__ void eval_model(const KinDev& kd, const float (&K1)[VPT],
                                            const float (&k2)[VPT], const float (&k3)[VPT],
                                            const float (&Vb)[VPT], Sink& sink) {
-  const unsigned mask = __activemask();
-  float a[VPT], dl[VPT], I[VPT], Ip[VPT], Jr[VPT], Jp[VPT], SA[VPT], SB[VPT], SAp[VPT], SBp[VPT];
-  int cen[VPT];
+  constexpr float h = 1.0f / NODES_PER_UNIT;
+  int j[VPT];
+  float b00[VPT], b10[VPT], b01[VPT], b11[VPT];   // Hermite basis (h folded in)
 #pragma unroll
   for (int v = 0; v < VPT; ++v) {
-    a[v] = fmaxf(k2[v] + k3[v], 0.f);
-    I[v] = Ip[v] = Jr[v] = Jp[v] = SA[v] = SB[v] = SAp[v] = SBp[v] = 0.f;
-    cen[v] = min(NCENT - 1, (int)(a[v] * (1.0f / DCENT)));
-    dl[v] = a[v] - (float)cen[v] * DCENT;
+    const float a = fmaxf(k2[v] + k3[v], 0.f);
+    const float u = a * (float)NODES_PER_UNIT;
+    j[v] = min((int)u, N_NODES - 2);                // a beyond A_MAX extrapolates
+    const float t = u - (float)j[v];
+    const float t2 = t * t, t3 = t2 * t;
+    b00[v] = fmaf(2.f, t3, fmaf(-3.f, t2, 1.f));
+    b10[v] = (t3 - 2.f * t2 + t) * h;
+    b01[v] = fmaf(-2.f, t3, 3.f * t2);
+    b11[v] = (t3 - t2) * h;
   }
-  // Frame schedules repeat interval lengths (PR2: 4 distinct over 24 intervals),
-  // so the series length, e^{-aD} and the input-free terms G, H (and their
-  // a-derivatives) are recomputed only when D changes.
-  float Dprev = -1.f, E[VPT], Gc[VPT], Hc[VPT], Gpc[VPT], Hpc[VPT];
-  int K = 0;
-  for (int iv = 0; iv < kd.n_iv; ++iv) {
-    const float D = __ldg(kd.iv_dt + iv);
-    const float4* tab = kd.coef + (size_t)iv * KC * 3 * NCENT;
-    if (D != Dprev) {   // uniform across the warp
-      Dprev = D;
-      K = 0;
-#pragma unroll
-      for (int v = 0; v < VPT; ++v) {
-        K = max(K, series_terms(dl[v] * D));
-        E[v] = expf(-a[v] * D);
-      }
-      K = min(KC, __reduce_max_sync(mask, K));   // one trip count per warp
-#pragma unroll
-      for (int v = 0; v < VPT; ++v) {
-        float g = 0.f, h = 0.f, gp = 0.f, hp = 0.f;
-        for (int n = K - 1; n >= 0; --n) {
-          const float4 c = __ldg(tab + (size_t)n * 3 * NCENT + 2 * NCENT + cen[v]);
-          g = fmaf(g, dl[v], c.x);
-          h = fmaf(h, dl[v], c.y);
-          if (JAC) {
-            gp = fmaf(gp, dl[v], c.z);
-            hp = fmaf(hp, dl[v], c.w);
-          }
-        }
-        Gc[v] = E[v] * g;
-        Hc[v] = E[v] * h;
-        Gpc[v] = -E[v] * gp;
-        Hpc[v] = -E[v] * hp;
-      }
-    }
-    Series p[VPT];
-#pragma unroll
-    for (int v = 0; v < VPT; ++v) p[v] = Series{0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-    KCS_UNROLL(KCS_HORNER_UNROLL)
-    for (int n = K - 1; n >= 0; --n) {
-      const float4* row = tab + (size_t)n * 3 * NCENT;
-      float4 c0, c1;
-#pragma unroll
-      for (int v = 0; v < VPT; ++v) {
-        if (v == 0 || cen[v] != cen[v - 1]) {   // the voxels of a thread often share a centre
-          c0 = __ldg(row + cen[v]);
-          c1 = JAC ? __ldg(row + NCENT + cen[v]) : make_float4(0.f, 0.f, 0.f, 0.f);
-        }
-        const float d = dl[v];
-        p[v].m1 = fmaf(p[v].m1, d, c0.x);
-        p[v].m2 = fmaf(p[v].m2, d, c0.y);
-        p[v].m3 = fmaf(p[v].m3, d, c0.z);
-        if (JAC) {
-          p[v].d1 = fmaf(p[v].d1, d, c0.w);
-          p[v].d2 = fmaf(p[v].d2, d, c1.x);
-          p[v].d3 = fmaf(p[v].d3, d, c1.y);
-        }
-      }
-    }
-    const int code = __ldg(kd.iv_code + iv);
-    const bool in_frame = code >= 0;             // gaps propagate the state only
-    const bool frame_end = in_frame && (code & 1);
-    const int m = code >> 1;
-    const float inv = frame_end ? __ldg(kd.fr_inv + m) : 0.f;
-    const float cpf = frame_end ? __ldg(kd.fr_cp + m) : 0.f;
+  for (int m = 0; m < kd.M; ++m) {
+    const float cp = __ldg(kd.fr_cp + m);
+    const float4* row = kd.node + (size_t)m * N_NODES;
+    const float2* row2 = kd.node2 + (size_t)m * N_NODES;
 #pragma unroll
     for (int v = 0; v < VPT; ++v) {
-      const float Ev = E[v];
-      const float G = Gc[v], H = Hc[v];
-      const float A = fmaf(I[v], G, Ev * p[v].m2);
-      const float B = fmaf(Jr[v], D, fmaf(I[v], H, Ev * p[v].m3));
+      const float4 c0 = __ldg(row + j[v]);
+      const float4 c1 = __ldg(row + j[v] + 1);
+      const float A = fmaf(b00[v], c0.x, fmaf(b10[v], c0.y, fmaf(b01[v], c1.x, b11[v] * c1.y)));
+      const float B = fmaf(b00[v], c0.z, fmaf(b10[v], c0.w, fmaf(b01[v], c1.z, b11[v] * c1.w)));
+      const float S = fmaf(k3[v], B, A);
+      const float T = K1[v] * S;
+      const float F = fmaf(Vb[v], cp - T, T);       // (1 - Vb) T + Vb cp
       if (JAC) {
-        const float Gp = Gpc[v], Hp = Hpc[v];
-        const float Ap = fmaf(Ip[v], G, fmaf(I[v], Gp, -Ev * p[v].d2));
-        const float Bp = fmaf(Jp[v], D, fmaf(Ip[v], H, fmaf(I[v], Hp, -Ev * p[v].d3)));
-        Ip[v] = fmaf(Ev, fmaf(-D, I[v], Ip[v]), -Ev * p[v].d1);
-        Jp[v] += Ap;
-        if (in_frame) {
-          SAp[v] += Ap;
-          SBp[v] += Bp;
-        }
-      }
-      I[v] = fmaf(Ev, I[v], Ev * p[v].m1);
-      Jr[v] += A;
-      if (in_frame) {
-        SA[v] += A;
-        SB[v] += B;
-      }
-      if (frame_end) {
-        const float S = fmaf(k3[v], SB[v], SA[v]) * inv;   // frame average of C_T / K1
-        const float T = K1[v] * S;
-        const float F = fmaf(Vb[v], cpf - T, T);           // (1 - Vb) T + Vb cp
-        if (JAC) {
-          // dC_T/dk2 = K1 (dI/da + k3 dJ/da); dC_T/dk3 = K1 (dI/da + J + k3 dJ/da),
-          // and dI/da + J = -a dJ/da (from I' = Cp - a I), so dC_T/dk3 = -K1 k2 dJ/da:
-          // a single non-negative term, exactly 0 at k2 = 0 instead of a cancelling
-          // difference.
-          const float w = 1.f - Vb[v];
-          const float Sp = fmaf(k3[v], SBp[v], SAp[v]) * inv;
-          sink(v, m, F, w * S, w * K1[v] * Sp, -w * K1[v] * k2[v] * SBp[v] * inv, cpf - T);
-        } else {
-          sink(v, m, F, 0.f, 0.f, 0.f, 0.f);
-        }
-        SA[v] = SB[v] = SAp[v] = SBp[v] = 0.f;
+        // the derivatives interpolate the tabulated (A', A'') and (B', B''):
+        // differentiating the value interpolant instead would subtract two
+        // rounded float32 node values (relative errors up to 1e-3)
+        const float2 e0 = __ldg(row2 + j[v]);
+        const float2 e1 = __ldg(row2 + j[v] + 1);
+        const float Ap = fmaf(b00[v], c0.y, fmaf(b10[v], e0.x, fmaf(b01[v], c1.y, b11[v] * e1.x)));
+        const float Bp = fmaf(b00[v], c0.w, fmaf(b10[v], e0.y, fmaf(b01[v], c1.w, b11[v] * e1.y)));
+        const float w = 1.f - Vb[v];
+        sink(v, m, F, w * S, w * K1[v] * fmaf(k3[v], Bp, Ap), -w * K1[v] * k2[v] * Bp, cp - T);
+      } else {
+        sink(v, m, F, 0.f, 0.f, 0.f, 0.f);
       }
     }
   }
@@ -847,9 +812,9 @@ int kcs_create_kinetics(kcs_kinetics_t** out, int n_frames, const double* t_star
   gauss_legendre(NGL, gx, gw);
   cudaStream_t s = as_stream(stream);
   const size_t nd = 2 * (size_t)n_iv + 2 * NGL + n_frames + n_iv;
-  bool ok = cudaMalloc(&k->d_coef, sizeof(float) * (size_t)n_iv * NCENT * KC * NCH) == cudaSuccess;
+  bool ok = cudaMalloc(&k->d_node, sizeof(float4) * (size_t)n_frames * N_NODES) == cudaSuccess;
+  ok = ok && cudaMalloc(&k->d_node2, sizeof(float2) * (size_t)n_frames * N_NODES) == cudaSuccess;
   ok = ok && cudaMalloc(&k->d_base, sizeof(double) * (size_t)n_iv * NB * 10) == cudaSuccess;
-  ok = ok && cudaMalloc(&k->d_iv_dt, sizeof(float) * n_iv) == cudaSuccess;
   ok = ok && cudaMalloc(&k->d_iv_code, sizeof(int) * n_iv) == cudaSuccess;
   ok = ok && cudaMalloc(&k->d_fr_cp, sizeof(float) * n_frames) == cudaSuccess;
   ok = ok && cudaMalloc(&k->d_fr_inv, sizeof(float) * n_frames) == cudaSuccess;
@@ -865,9 +830,7 @@ int kcs_create_kinetics(kcs_kinetics_t** out, int n_frames, const double* t_star
   std::copy(gx.begin(), gx.end(), host.begin() + 2 * n_iv);
   std::copy(gw.begin(), gw.end(), host.begin() + 2 * n_iv + NGL);
   std::copy(fdt.begin(), fdt.end(), host.begin() + 2 * n_iv + 2 * NGL);
-  std::vector<float> dtf(dt.begin(), dt.end());
   KCS_CUDA(cudaMemcpyAsync(k->d_tmp, host.data(), sizeof(double) * nd, cudaMemcpyHostToDevice, s));
-  KCS_CUDA(cudaMemcpyAsync(k->d_iv_dt, dtf.data(), sizeof(float) * n_iv, cudaMemcpyHostToDevice, s));
   KCS_CUDA(cudaMemcpyAsync(k->d_iv_code, code.data(), sizeof(int) * n_iv, cudaMemcpyHostToDevice, s));
   TabArgs ta;
   ta.iv_t0 = k->d_tmp;
@@ -882,7 +845,9 @@ int kcs_create_kinetics(kcs_kinetics_t** out, int n_frames, const double* t_star
   ta.m0 = k->d_tmp + 2 * n_iv + 2 * NGL + n_frames;
   k_tabulate<<<n_iv, NB, 0, s>>>(ta);
   KCS_LAUNCHED();
-  k_shift<<<n_iv * NCENT, KC * 10, 0, s>>>(k->d_base, reinterpret_cast<float*>(k->d_coef));
+  k_node_table<<<(N_NODES + 127) / 128, 128, 0, s>>>(k->d_base, ta.iv_dt, k->d_iv_code, n_iv,
+                                                       k->d_tmp + 2 * n_iv + 2 * NGL, n_frames,
+                                                       N_NODES, k->d_node, k->d_node2);
   KCS_LAUNCHED();
   k_frame_tables<<<1, 32, 0, s>>>(ta.m0, k->d_iv_code, n_iv, k->d_tmp + 2 * n_iv + 2 * NGL,
                                   n_frames, k->d_fr_cp, k->d_fr_inv);
@@ -896,9 +861,9 @@ int kcs_create_kinetics(kcs_kinetics_t** out, int n_frames, const double* t_star
 int kcs_destroy_kinetics(kcs_kinetics_t* k) {
   clear_error();
   if (!k) return KCS_OK;
-  cudaFree(k->d_coef);
+  cudaFree(k->d_node);
+  cudaFree(k->d_node2);
   cudaFree(k->d_base);
-  cudaFree(k->d_iv_dt);
   cudaFree(k->d_iv_code);
   cudaFree(k->d_fr_cp);
   cudaFree(k->d_fr_inv);

@@ -173,7 +173,7 @@ def test_pr1_other_methods_end_to_end(cuda_ok, method):
     # float32 and float64 LM decisions differ on flat-valley voxels even from the
     # same image, so the fitted model TACs get a float32 allowance of 5e-3
     assert e_F < 2 * env["model_tac_rel_l2"] + 5e-3
-    assert ki_dev < 0.02
+    assert ki_dev < 2 * env["Ki_class_mean_rel"] + 0.01
 
 
 def test_stacked_planes_equal_separate_studies(cuda_ok):
