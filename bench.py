@@ -75,9 +75,9 @@ LM_FLOPS_PER_VOXEL_STEP = lm_flops_per_voxel_step(frames=S.WORKLOADS["pr2"].n_fr
 # planes: every kernel touches each plane's data independently), valid while
 # the kernel's source file is unchanged (sha256 prefix); see profiles/.
 TRAFFIC = {
-    "lm_step": {"bytes": 469.39e6 * 127 / 16, "src": "kinetics.cu", "sha": "19be0745b272f8ce"},
-    "bwd_osl": {"bytes": 506.51e6 * 127 / 16, "src": "projector.cu", "sha": "0512c95270c997be"},
-    "fwd_ratio": {"bytes": 258.78e6 * 127 / 16, "src": "projector.cu", "sha": "0512c95270c997be"},
+    "lm_step": {"bytes": 471.02e6 * 127 / 16, "src": "kinetics.cu", "sha": "1976f407e435edd3"},
+    "bwd_osl": {"bytes": 506.56e6 * 127 / 16, "src": "projector.cu", "sha": "7e72329affffd00c"},
+    "fwd_ratio": {"bytes": 254.37e6 * 127 / 16, "src": "projector.cu", "sha": "7e72329affffd00c"},
 }
 
 
