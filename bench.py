@@ -15,7 +15,9 @@ series (1.44 GB) and the counts (1.06 GB) are larger than the 126 MB L2.
 
 --storage bf16 / f16 runs the precision form: image series and ratio
 sinograms stored in bfloat16 / float16 with a per-frame scale (max of the start
-image), counts as uint16; arithmetic stays float32.  The default is float32.
+image); arithmetic stays float32.  The default is float32.  The measured
+counts are integers and are held as uint16 by default (exact; --counts f32
+for float32 counts, bit-identical results).
 
 --impl reference times the FP64 CPU oracle on a bounded sample of the same
 workload (one plane, one subset update, one LM step on 4096 voxels) and
@@ -278,9 +280,12 @@ def run_ours(args):
     M = W.n_frames
     sdt = {"f32": torch.float32, "bf16": torch.bfloat16, "f16": torch.float16}[args.storage]
     x_scale = None
-    if args.storage != "f32":
+    if args.counts == "u16" or args.storage != "f32":
+        # measured counts are integers: uint16 holds them exactly (same results
+        # bit for bit as float32 counts) at half the bytes
         assert counts.max().item() < 65536
         counts = counts.to(torch.uint16)
+    if args.storage != "f32":
         x_scale = K.init_level(g, dt, kappa, counts, r)     # the start image's per-frame level
     x = K.init_image(g, dt, kappa, counts, r, dtype=sdt, x_scale=x_scale)
     params = torch.empty((4, W.nz, W.ny, W.nx), device=dev)
@@ -360,7 +365,7 @@ def run_ours(args):
     hbm, smax, src = _peaks()
     V = W.nx * W.ny * W.nz
     es = 4 if args.storage == "f32" else 2                 # stored image / ratio element
-    cs = 4 if args.storage == "f32" else 2                 # counts element
+    cs = counts.element_size()                             # counts element
     img = V * M * es
     img32 = V * M * 4                                      # F (model TACs) stays float32
     n_sub = W.n_angles // W.n_subsets
@@ -407,7 +412,8 @@ def run_ours(args):
                    "voxels": V, "frames": M, "subsets": S_, "lm_steps": N_LM,
                    "l2": f"inputs larger than L2 (image series {img / 1e9:.2f} GB, counts "
                          f"{W.nz * W.n_angles * W.n_bins * M * cs / 1e9:.2f} GB)",
-                   "storage": ("float32" if args.storage == "f32" else
+                   "storage": (f"float32 image and ratio, {'uint16' if cs == 2 else 'float32'} "
+                               "counts" if args.storage == "f32" else
                                f"{args.storage} image and ratio with per-frame scale, uint16 counts"),
                    "randoms": "uniform per frame", "beta_kp": beta_kp, "beta_h": BETA_H,
                    "delta": DELTA},
@@ -665,6 +671,8 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--storage", choices=["f32", "bf16", "f16"], default="f32")
+    ap.add_argument("--counts", choices=["u16", "f32"], default="u16",
+                    help="storage of the measured counts (integers: uint16 is exact)")
     ap.add_argument("--planes", type=int, default=127,
                     help="central planes of the workload (127 = full; fewer for profiler captures)")
     ap.add_argument("--serve", action="store_true",
