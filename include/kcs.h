@@ -191,12 +191,16 @@ int kcs_init_image_ex(const kcs_geometry_t* g, int n_frames, const float* frame_
  * parameters (K1, k2, k3, Vb), a = k2 + k3, driven by the Feng plasma input
  *   Cp(t) = (A1 t - A2 - A3) e^{-l1 t} + A2 e^{-l2 t} + A3 e^{-l3 t},
  *   F_m = (1/dt_m) int_{frame m} [(1 - Vb) C_T + Vb Cp] dt,
- * evaluated analytically (Sec. II-C): per interval the convolution with
- * e^{-at} is e^{-aD} times a power series in a with non-negative coefficients
- * (input moments over the interval) that this call tabulates once in float64
- * on the device.  t_start, t_end: host arrays of n_frames frame limits
- * (ordered, no overlap; gaps allowed); feng: host {A1, A2, A3, l1, l2, l3}.
- * Valid for 0 <= k2 + k3 <= 3.5 per minute (the LM box reaches 3). */
+ * evaluated analytically (Sec. II-C).  With a fixed the model is linear in
+ * K1, k3, Vb: F_m = (1 - Vb) K1 (A_m(a) + k3 B_m(a)) + Vb cp_m.  This call
+ * tabulates A_m, B_m and their first and second a-derivatives once, in
+ * float64 on the device, on a grid of a (spacing 1/512 per minute), from the
+ * exact interval-by-interval convolution (per interval e^{-aD} times a power
+ * series in a with non-negative input-moment coefficients); evaluations
+ * interpolate that table (cubic Hermite, ~1e-8 of each frame's range).
+ * t_start, t_end: host arrays of n_frames frame limits (ordered, no overlap;
+ * gaps allowed); feng: host {A1, A2, A3, l1, l2, l3}.  Valid for
+ * 0 <= k2 + k3 <= 3.75 per minute (the LM box reaches 3).  Synchronous. */
 int kcs_create_kinetics(kcs_kinetics_t** out, int n_frames, const double* t_start,
                         const double* t_end, const double* feng, void* stream);
 int kcs_destroy_kinetics(kcs_kinetics_t* k);
