@@ -131,7 +131,6 @@ struct kcs_kinetics {
   float4* d_node;
   float2* d_node2;
   float* d_fr_cp;
-  float* d_fr_inv;
   int* d_iv_code;
   double* d_tmp;   // per-interval doubles used while tabulating
   double* d_base;  // [n_iv][NB][10] float64 base series

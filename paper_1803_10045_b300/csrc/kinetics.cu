@@ -188,14 +188,13 @@ __global__ void k_node_table(const double* base, const double* iv_dt, const int*
 }
 
 __global__ void k_frame_tables(const double* m0, const int* code, int n_iv, const double* fdt,
-                               int M, float* fr_cp, float* fr_inv) {
+                               int M, float* fr_cp) {
   const int m = blockIdx.x * blockDim.x + threadIdx.x;
   if (m >= M) return;
   double s = 0.0;
   for (int i = 0; i < n_iv; ++i)
     if (code[i] >= 0 && (code[i] >> 1) == m) s += m0[i];
   fr_cp[m] = (float)(s / fdt[m]);
-  fr_inv[m] = (float)(1.0 / fdt[m]);
 }
 
 // ---------------------------------------------------------------- model
@@ -817,7 +816,6 @@ int kcs_create_kinetics(kcs_kinetics_t** out, int n_frames, const double* t_star
   ok = ok && cudaMalloc(&k->d_base, sizeof(double) * (size_t)n_iv * NB * 10) == cudaSuccess;
   ok = ok && cudaMalloc(&k->d_iv_code, sizeof(int) * n_iv) == cudaSuccess;
   ok = ok && cudaMalloc(&k->d_fr_cp, sizeof(float) * n_frames) == cudaSuccess;
-  ok = ok && cudaMalloc(&k->d_fr_inv, sizeof(float) * n_frames) == cudaSuccess;
   ok = ok && cudaMalloc(&k->d_tmp, sizeof(double) * nd) == cudaSuccess;
   if (!ok) {
     set_error("cudaMalloc failed for kinetics tables");
@@ -850,7 +848,7 @@ int kcs_create_kinetics(kcs_kinetics_t** out, int n_frames, const double* t_star
                                                        N_NODES, k->d_node, k->d_node2);
   KCS_LAUNCHED();
   k_frame_tables<<<1, 32, 0, s>>>(ta.m0, k->d_iv_code, n_iv, k->d_tmp + 2 * n_iv + 2 * NGL,
-                                  n_frames, k->d_fr_cp, k->d_fr_inv);
+                                  n_frames, k->d_fr_cp);
   KCS_LAUNCHED();
   // the host staging vectors die here: wait for the copies
   KCS_CUDA(cudaStreamSynchronize(s));
@@ -866,7 +864,6 @@ int kcs_destroy_kinetics(kcs_kinetics_t* k) {
   cudaFree(k->d_base);
   cudaFree(k->d_iv_code);
   cudaFree(k->d_fr_cp);
-  cudaFree(k->d_fr_inv);
   cudaFree(k->d_tmp);
   delete k;
   return KCS_OK;
