@@ -206,7 +206,8 @@ int kcs_create_kinetics(kcs_kinetics_t** out, int n_frames, const double* t_star
 int kcs_destroy_kinetics(kcs_kinetics_t* k);
 
 /* F = model TACs of n_vox voxels: params [4][n_vox] -> F [n_vox][M];
- * J [n_vox][M][4] (d/dK1, d/dk2, d/dk3, d/dVb) when not NULL. */
+ * J [n_vox][M][4] (d/dK1, d/dk2, d/dk3, d/dVb) when not NULL.  n_vox = 0 is a
+ * no-op (the pointers may then be NULL); so for kcs_tac_vjp and kcs_ki. */
 int kcs_tac_eval(const kcs_kinetics_t* k, int64_t n_vox, const float* params, float* F,
                  float* J, void* stream);
 /* Reverse mode of kcs_tac_eval: gparams[q][v] = sum_m dF_vm/dxi_q * gF[v][m]

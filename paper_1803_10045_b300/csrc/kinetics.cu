@@ -872,17 +872,19 @@ int kcs_destroy_kinetics(kcs_kinetics_t* k) {
 int kcs_tac_eval(const kcs_kinetics_t* k, int64_t n_vox, const float* params, float* F, float* J,
                  void* stream) {
   clear_error();
-  KCS_REQUIRE(k && params && F, "NULL argument");
+  KCS_REQUIRE(k, "kinetics is NULL");
   KCS_REQUIRE(n_vox >= 0, "n_vox < 0");
+  KCS_REQUIRE(n_vox == 0 || (params && F), "NULL argument");
   return launch_tac_eval(k, n_vox, params, F, J, as_stream(stream));
 }
 
 int kcs_tac_vjp(const kcs_kinetics_t* k, int64_t n_vox, const float* params, const float* gF,
                 float* gparams, void* stream) {
   clear_error();
-  KCS_REQUIRE(k && params && gF && gparams, "NULL argument");
+  KCS_REQUIRE(k, "kinetics is NULL");
   KCS_REQUIRE(n_vox >= 0, "n_vox < 0");
   if (n_vox == 0) return KCS_OK;
+  KCS_REQUIRE(params && gF && gparams, "NULL argument");
   const size_t smem = sizeof(float) * TAC_THREADS * (k->M + 1);
   k_tac_vjp<<<(unsigned)((n_vox + TAC_THREADS - 1) / TAC_THREADS), TAC_THREADS, smem,
               as_stream(stream)>>>(k->dev(), n_vox, params, gF, gparams);
@@ -892,9 +894,9 @@ int kcs_tac_vjp(const kcs_kinetics_t* k, int64_t n_vox, const float* params, con
 
 int kcs_ki(int64_t n_vox, const float* params, float* ki, void* stream) {
   clear_error();
-  KCS_REQUIRE(params && ki, "NULL argument");
   KCS_REQUIRE(n_vox >= 0, "n_vox < 0");
   if (n_vox == 0) return KCS_OK;
+  KCS_REQUIRE(params && ki, "NULL argument");
   k_ki<<<(unsigned)((n_vox + 255) / 256), 256, 0, as_stream(stream)>>>(n_vox, params, ki);
   KCS_LAUNCHED();
   return KCS_OK;

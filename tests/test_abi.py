@@ -60,3 +60,13 @@ def test_workspace_sizes_without_gpu():
     from paper_1803_10045_b300._lib import lib
     assert lib.kcs_lm_workspace_size(10, 10, 2) >= 5 * 200 * 4
     assert lib.kcs_lm_workspace_size(0, 10, 2) == 0
+
+
+def test_empty_voxel_sets_need_no_buffers():
+    """n_vox = 0 is a no-op for the per-voxel kinetics calls: NULL buffers are
+    accepted without touching a device (the kinetics handle is still required)."""
+    import ctypes as C
+    from paper_1803_10045_b300._lib import lib
+    assert lib.kcs_ki(0, None, None, None) == 0
+    assert lib.kcs_ki(-1, None, None, None) != 0
+    assert lib.kcs_tac_eval(None, 0, None, None, None, None) != 0      # no kinetics handle

@@ -231,3 +231,22 @@ def test_checkpoint_resume_is_bit_identical(cuda_ok, tmp_path, storage):
     c.iterate(2)
     torch.cuda.synchronize()
     assert torch.equal(a.x, c.x) and torch.equal(a.params, c.params) and torch.equal(a.F, c.F)
+
+
+def test_degenerate_inputs_stay_finite(cuda_ok):
+    """All-zero counts (no measured events) and a study whose planes hold no
+    activity: the ICM keeps every output finite and the maps inside the box."""
+    K, P, W, kg, kin = _setup()
+    dt = _t(_f32(P["dt"]))
+    kappa = float(np.float32(P["kappa"]))
+    for counts in (torch.zeros(kg.sino_shape(W.n_frames), device="cuda"), _t(P["counts"])):
+        x = K.init_image(kg, dt, kappa, counts)
+        params = _t(np.broadcast_to(np.array(S.XI0)[:, None, None, None], (4, 1, W.ny, W.nx)))
+        st = K.Study(kg, kin, dt, kappa, counts, x, params, n_lm=10, beta_kp=0.1, beta_h=0.1,
+                     delta=0.01)
+        st.iterate(2)
+        torch.cuda.synchronize()
+        for t in (x, params, st.F):
+            assert torch.isfinite(t).all()
+        hi = torch.tensor([2.0, 2.0, 1.0, 1.0], device="cuda")[:, None, None, None]
+        assert (params >= 0).all() and (params <= hi).all()
