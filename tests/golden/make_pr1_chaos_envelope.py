@@ -2,7 +2,7 @@
 on config PR1 moves when the count calibration kappa is perturbed by 1e-5
 (relative), and when its image and ratio are stored in bfloat16 / float16.  ICM with MAP-LM is sensitive to perturbations of the data (LM
 decisions at the edge of a decrease, voxels switching between local minima),
-so an end-to-end float32 run is judged against this envelope.  Calls only the
+so an end-to-end float32 run is compared with this envelope.  Calls only the
 oracle.  Run from the repository root: python tests/golden/make_pr1_chaos_envelope.py
 """
 import json

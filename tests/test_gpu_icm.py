@@ -136,7 +136,7 @@ def test_pr1_other_methods_end_to_end(cuda_ok, method):
     """INDIRECT (OSEM then one post-reconstruction fit) and DIRECT (no spatial
     prior in the fit) against the oracle's same method (Sec. IV-A).  The OSEM
     image of INDIRECT is deterministic and contractive, so it is held to the
-    image tolerance; the fitted outputs are judged against the oracle's own
+    image tolerance; the fitted outputs are compared with the oracle's own
     sensitivity envelope for that method."""
     K, P, W, kg, kin = _setup()
     dt = _f32(P["dt"])
