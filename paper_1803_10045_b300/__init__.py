@@ -5,7 +5,9 @@ updates with a kinetics-derived prior and a voxel-parallel MAP
 Levenberg-Marquardt fit of the FDG two-tissue model under a Huber MRF prior --
 as hand-written sm_103a CUDA kernels behind the C ABI of include/kcs.h
 (libkcs.so).  This package is the thin Python binding: it marshals torch CUDA
-tensors into that ABI and has no CPU fallback.
+tensors into that ABI and has no CPU fallback.  Around it: the differentiable
+forward model (autograd), a serving loop for many studies under an HBM budget
+(serving), and plane sharding across ranks (sharding).
 """
 from ._lib import LIB_PATH, KcsError, lib  # noqa: F401
 from .api import (  # noqa: F401
