@@ -300,7 +300,9 @@ def run_ours(args):
 
     # ---- timed region: the kernels icm_iterate issues, with events between them
     S_ = W.n_subsets
-    rhos = {g.n_sub(k): torch.empty(g.sino_shape(M, k), device=dev, dtype=sdt) for k in range(S_)}
+    # ratio rows at the padded pitch the fused OSL update uses internally
+    rhos = {g.n_sub(k): torch.empty(g.sino_shape(K.rho_frames(M, sdt), k), device=dev, dtype=sdt)
+            for k in range(S_)}
     lm_ws = torch.empty(K.lm_workspace_size(W.nx, W.ny, W.nz), dtype=torch.uint8, device=dev)
 
     def ev():

@@ -140,15 +140,25 @@ int kcs_osl_backproject(const kcs_geometry_t* g, int subset, int n_frames, const
                         void* stream);
 /* Precision form of the three calls above: counts stored as counts_type, the
  * image x as x_type with per-frame scale x_scale, and the ratio rho (or the
- * workspace holding it) stored as x_type; projections and updates are float32. */
+ * workspace holding it) stored as x_type; projections and updates are float32.
+ * The split calls also take the row pitch of rho: rho is [Z][A_k][B][rho_frames]
+ * with frames 0..n_frames-1 of each row used, rho_frames a multiple of 4 in
+ * [n_frames, 256] (n_frames: dense rows, as in the plain calls). */
 int kcs_osl_ratio_ex(const kcs_geometry_t* g, int subset, int n_frames, const float* frame_dt,
                      float kappa, const void* counts, int counts_type, const float* randoms,
                      int randoms_layout, const float* bin_factor, const void* x, int x_type,
-                     const float* x_scale, void* rho, void* stream);
+                     const float* x_scale, void* rho, int rho_frames, void* stream);
 int kcs_osl_backproject_ex(const kcs_geometry_t* g, int subset, int n_frames,
                            const float* frame_dt, float kappa, const float* bin_factor,
-                           const void* rho, const float* F_model, float beta_kp, float sigma2,
-                           void* x, int x_type, const float* x_scale, void* stream);
+                           const void* rho, int rho_frames, const float* F_model, float beta_kp,
+                           float sigma2, void* x, int x_type, const float* x_scale,
+                           void* stream);
+/* The row pitch (frames) of the ratio kcs_osl_update keeps in its workspace,
+ * and the fastest for the split calls: for KCS_F32 an odd number of 4-frame
+ * quads (n_frames + 4 when n_frames / 4 is even), so that the back-projection's
+ * 16-byte shared-memory reads of up to 8 consecutive bins hit distinct bank
+ * groups; n_frames for 16-bit storage.  Pure function, no GPU work. */
+int kcs_osl_rho_frames(int n_frames, int x_type);
 int kcs_osl_update_ex(const kcs_geometry_t* g, int subset, int n_frames, const float* frame_dt,
                       float kappa, const void* counts, int counts_type, const float* randoms,
                       int randoms_layout, const float* bin_factor, const float* F_model,

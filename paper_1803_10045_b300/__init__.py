@@ -14,5 +14,5 @@ from .api import (  # noqa: F401
     RANDOMS_FULL, RANDOMS_NONE, RANDOMS_PER_FRAME, Geometry, Kinetics, Study, back_project,
     device_status,
     forward_project, huber_grad, init_image, init_level, ki, loglik, lm_workspace_size, map_lm_fit, osl_backproject,
-    osl_ratio, osl_update, osl_workspace_size, sensitivity, tac_eval)
+    osl_ratio, osl_update, osl_workspace_size, rho_frames, sensitivity, tac_eval)
 from .autograd import KineticForward, forward_model, tac_vjp  # noqa: F401,E402

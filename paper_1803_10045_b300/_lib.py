@@ -59,8 +59,11 @@ SIGNATURES = {
     "kcs_osl_ratio": (i32, [vp, i32, i32, vp, f32, vp, vp, i32, vp, vp, vp, vp]),
     "kcs_osl_backproject": (i32, [vp, i32, i32, vp, f32, vp, vp, vp, f32, f32, vp, vp]),
     "kcs_init_image": (i32, [vp, i32, vp, f32, vp, vp, i32, vp, vp, vp, sz, vp]),
-    "kcs_osl_ratio_ex": (i32, [vp, i32, i32, vp, f32, vp, i32, vp, i32, vp, vp, i32, vp, vp, vp]),
-    "kcs_osl_backproject_ex": (i32, [vp, i32, i32, vp, f32, vp, vp, vp, f32, f32, vp, i32, vp, vp]),
+    "kcs_osl_ratio_ex": (i32, [vp, i32, i32, vp, f32, vp, i32, vp, i32, vp, vp, i32, vp, vp, i32,
+                               vp]),
+    "kcs_osl_backproject_ex": (i32, [vp, i32, i32, vp, f32, vp, vp, i32, vp, f32, f32, vp, i32, vp,
+                                     vp]),
+    "kcs_osl_rho_frames": (i32, [i32, i32]),
     "kcs_osl_update_ex": (i32, [vp, i32, i32, vp, f32, vp, i32, vp, i32, vp, vp, f32, f32, vp, i32,
                                 vp, vp, sz, vp]),
     "kcs_loglik": (i32, [vp, i32, vp, f32, vp, i32, vp, i32, vp, vp, i32, vp, vp, vp, sz, vp]),

@@ -162,36 +162,49 @@ def osl_update(g: Geometry, subset, x, frame_dt, kappa, counts, randoms=None, bi
     return x
 
 
+def rho_frames(M, dtype=torch.float32):
+    """Row pitch (frames) of the ratio rows that osl_update keeps internally and
+    that osl_ratio allocates by default: M padded to an odd number of 4-frame
+    quads for float32, M for 16-bit storage."""
+    return lib.kcs_osl_rho_frames(int(M), _STORAGE.get(dtype, F32))
+
+
 def osl_ratio(g: Geometry, subset, x, frame_dt, kappa, counts, randoms=None, bin_factor=None,
               out=None, x_scale=None):
-    """rho = s / ybar on the rays of subset k: [Z][A_k][B][M], stored in x's
-    dtype (float32, bfloat16 or float16; x holds x / x_scale[m])."""
+    """rho = s / ybar on the rays of subset k, stored in x's dtype (float32,
+    bfloat16 or float16; x holds x / x_scale[m]): out [Z][A_k][B][P] with the
+    ratio in frames [..., :M]; P = rho_frames(M, dtype) by default, or out's
+    own last dimension (a multiple of 4, >= M; M gives dense rows)."""
     M = x.shape[-1]
     pr, layout = _randoms(g, randoms, M)
     xt = _storage(x, (F32, BF16, F16), "x")
     ct = _storage(counts, (F32, U16), "counts")
     if out is None:
-        out = torch.empty(g.sino_shape(M, subset), device=x.device, dtype=x.dtype)
+        out = torch.empty(g.sino_shape(rho_frames(M, x.dtype), subset), device=x.device,
+                          dtype=x.dtype)
+    P = out.shape[-1]
     check(lib.kcs_osl_ratio_ex(
         g.handle, subset, M, _ptr(frame_dt, "frame_dt", (M,)), float(kappa),
         _ptr(counts, "counts", g.sino_shape(M), dtype=counts.dtype), ct, pr, layout,
         _ptr(bin_factor, "bin_factor", (g.nz, g.n_angles, g.n_bins), allow_none=True),
         _ptr(x, "x", g.image_shape(M), dtype=x.dtype), xt,
         _ptr(x_scale, "x_scale", (M,), allow_none=True),
-        _ptr(out, "rho", g.sino_shape(M, subset), dtype=x.dtype), _stream()))
+        _ptr(out, "rho", g.sino_shape(P, subset), dtype=x.dtype), P, _stream()))
     return out
 
 
 def osl_backproject(g: Geometry, subset, x, frame_dt, kappa, rho, bin_factor=None, F=None,
                     beta=0.0, sigma2=1.0, x_scale=None):
     """OSL update of x (in place) from a ratio sinogram rho of subset k (rho in
-    x's dtype)."""
+    x's dtype, [Z][A_k][B][P] with the ratio in frames [..., :M], as osl_ratio
+    writes it)."""
     M = x.shape[-1]
     xt = _storage(x, (F32, BF16, F16), "x")
+    P = rho.shape[-1]
     check(lib.kcs_osl_backproject_ex(
         g.handle, subset, M, _ptr(frame_dt, "frame_dt", (M,)), float(kappa),
         _ptr(bin_factor, "bin_factor", (g.nz, g.n_angles, g.n_bins), allow_none=True),
-        _ptr(rho, "rho", g.sino_shape(M, subset), dtype=x.dtype),
+        _ptr(rho, "rho", g.sino_shape(P, subset), dtype=x.dtype), P,
         _ptr(F, "F", g.image_shape(M), allow_none=True), float(beta), float(sigma2),
         _ptr(x, "x", g.image_shape(M), dtype=x.dtype), xt,
         _ptr(x_scale, "x_scale", (M,), allow_none=True), _stream()))

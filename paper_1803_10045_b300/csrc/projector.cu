@@ -107,6 +107,7 @@ struct ProjArgs {
   void* xout;             // image output (back-projection)
   const void* y;          // subset sinogram input (back-projection), storage type TY
   void* yout;             // subset sinogram output (forward)
+  int yq;                 // 4-frame quads per bin row of y / yout (MQ: dense rows)
   const float4* xscale;   // per-frame scale of a stored image [MQ] (null: 1)
   const AngleTab* ang;
   const int* sub;         // angle indices of the subset
@@ -195,7 +196,7 @@ __global__ void __launch_bounds__(256) k_forward(ProjArgs p) {
   }
   acc.x *= T.w; acc.y *= T.w; acc.z *= T.w; acc.w *= T.w;
   if (p.xscale) acc = mul4(acc, __ldg(p.xscale + q));     // stored image -> activity
-  const size_t oi = ((size_t)(z * p.n_sub + ak) * p.B + b) * MQ + q;
+  const size_t oi = ((size_t)(z * p.n_sub + ak) * p.B + b) * p.yq + q;
   if (!RATIO) {
     st4(static_cast<TY*>(p.yout) + oi * 4, acc);
     return;
@@ -334,12 +335,12 @@ __global__ void __launch_bounds__(BK_TILE * BK_TILE) k_back_tiled(ProjArgs p, in
     __syncthreads();
     for (int c = 0; c < na; ++c) {
       const TY* src = static_cast<const TY*>(p.y) +
-                      ((size_t)(z * p.n_sub + a0 + c) * p.B + s_lo[c]) * MQ * 4;
+                      ((size_t)(z * p.n_sub + a0 + c) * p.B + s_lo[c]) * p.yq * 4;
       float4* dst = srho + (size_t)c * rows_max * PITCH;
       const int n = s_cnt[c] * MQ;
       for (int e = threadIdx.x; e < n; e += BK_TILE * BK_TILE) {
         const int r = e / MQ, q = e - r * MQ;
-        dst[r * PITCH + q] = load4(src + (size_t)e * 4);
+        dst[r * PITCH + q] = load4(src + ((size_t)r * p.yq + q) * 4);
       }
     }
     __syncthreads();
@@ -484,8 +485,8 @@ __global__ void k_selftest_wait(int limit) {
 template <int MQ, int MODE, class TX, class TY>
 __global__ void __launch_bounds__(BK_TILE * BK_TILE) k_back_bulk(ProjArgs p, int rows_max,
                                                                   int achunk) {
-  constexpr int RB = MQ * 4 * (int)sizeof(TY);   // bytes of one bin's frames
-  static_assert(RB % 16 == 0, "bulk copies move multiples of 16 bytes");
+  // bytes of one bin row: p.yq quads, a multiple of 16 (checked by the launcher)
+  const int RB = p.yq * 4 * (int)sizeof(TY);
   extern __shared__ __align__(16) unsigned char sraw[];   // [achunk][rows_max] rows
   __shared__ int s_lo[BK_ACHUNK], s_cnt[BK_ACHUNK], s_a[BK_ACHUNK];
   __shared__ AngleTab s_T[BK_ACHUNK];
@@ -590,7 +591,7 @@ __global__ void __launch_bounds__(BK_TILE * BK_TILE) k_back_bulk(ProjArgs p, int
         if (wt == 0.0f) continue;
         wt *= T.w;
         if (MODE == 1 && p.bin_factor) wt *= __ldg(p.bin_factor + binrow + b);
-        const TY* row = rows + (size_t)(b - lo) * MQ * 4;
+        const TY* row = rows + (size_t)(b - lo) * p.yq * 4;
 #pragma unroll
         for (int q = 0; q < MQ; ++q) fma4(acc[q], wt, ld4(row + q * 4));
         sens += wt;
@@ -738,6 +739,11 @@ static int check_geom(const kcs_geometry* g, int subset, int n_frames) {
 }
 
 static bool aligned16(const void* p) { return ((uintptr_t)p & 15u) == 0; }
+// Quads per bin row of the ratio kept in the OSL workspace: float rows get an
+// odd number of 16-byte quads so that the back-projection's 128-bit reads of
+// up to 8 consecutive bins fall in distinct shared-memory bank groups (a
+// 96-byte pitch repeats them every 4 bins); 16-bit rows stay dense.
+static int rho_pitch(int MQ, int x_type) { return x_type == KCS_F32 ? (MQ | 1) : MQ; }
 
 static ProjArgs base_args(const kcs_geometry* g, int subset) {
   ProjArgs p{};
@@ -749,7 +755,9 @@ static ProjArgs base_args(const kcs_geometry* g, int subset) {
 }
 
 template <bool RATIO, class TX, class TC, class TY>
-static void launch_forward_t(int MQ, const ProjArgs& p, cudaStream_t s) {
+static void launch_forward_t(int MQ, const ProjArgs& p0, cudaStream_t s) {
+  ProjArgs p = p0;
+  if (!p.yq) p.yq = MQ;
   const int rpw = 32 / MQ;
   const long long rays = (long long)p.nz * p.n_sub * p.B;
   const long long warps = (rays + rpw - 1) / rpw;
@@ -784,11 +792,12 @@ static void launch_ratio(int MQ, int tx, int tc, const ProjArgs& p, cudaStream_t
   else launch_ratio_tx<float>(MQ, tc, p, s);
 }
 
-// Rows of one angle a 16 x 16 tile can touch: the candidate span over the tile
-// (15 steps along both axes plus the +-1 interpolation band) divided by the
-// smallest |beta| (= bin / vox), plus the margins of bin_range and the union.
+// Rows of one angle a 16 x 16 tile can touch: over the tile's corners the
+// continuous bin coordinate moves by 15 (|cos| + |sin|) <= 15 sqrt(2) voxels
+// and the +-1 interpolation band adds 2 (in bins: times vox / bin); the floor
+// and ceiling, the margins of bin_range and the union add at most 7 rows.
 static int back_rows_max(const kcs_geometry* g) {
-  const double span = (BK_TILE - 1) * 2.0 + 2.0;
+  const double span = (BK_TILE - 1) * 1.41421357 + 2.0;
   return (int)std::ceil(span * g->vox / g->bin) + 8;
 }
 
@@ -799,9 +808,11 @@ constexpr size_t BK_SMEM_MAX = 200 * 1024;   // dynamic shared memory budget per
 #endif
 
 template <int MQ, int MODE, class TX, class TY>
-static int launch_back_mq(const ProjArgs& p, int rows_max, cudaStream_t s) {
-  if constexpr (KCS_BACK_BULK && (MQ * 4 * sizeof(TY)) % 16 == 0) {
-    const size_t row_bytes = (size_t)MQ * 4 * sizeof(TY) * rows_max;
+static int launch_back_mq(const ProjArgs& p0, int rows_max, cudaStream_t s) {
+  ProjArgs p = p0;
+  if (!p.yq) p.yq = MQ;
+  if (KCS_BACK_BULK && (p.yq * 4 * sizeof(TY)) % 16 == 0) {
+    const size_t row_bytes = (size_t)p.yq * 4 * sizeof(TY) * rows_max;
     const int achunk = (int)std::min<size_t>(BK_ACHUNK, BK_SMEM_MAX / row_bytes);
     KCS_REQUIRE(achunk >= 1, "bins are too fine relative to voxels for the tiled back-projection");
     const size_t smem = row_bytes * achunk;
@@ -993,7 +1004,8 @@ int kcs_sensitivity(const kcs_geometry_t* g, int subset, const float* bin_factor
 
 size_t kcs_osl_workspace_size(const kcs_geometry_t* g, int n_frames) {
   if (!g || n_frames <= 0) return 0;
-  const size_t rho = (size_t)g->nz * g->max_sub * g->B * n_frames * sizeof(float);
+  const size_t rho = (size_t)g->nz * g->max_sub * g->B * rho_pitch(n_frames / 4, KCS_F32) * 4 *
+                     sizeof(float);
   const size_t red = align256(sizeof(double) * RED_BLOCKS * (2 * (size_t)n_frames + 1)) +
                      align256(sizeof(double) * RED_BLOCKS) + align256(sizeof(float) * 32) +
                      align256((size_t)g->nz * g->ny * g->nx * sizeof(float));
@@ -1005,11 +1017,10 @@ static bool aligned_for(const void* ptr, int t) {
   return ((uintptr_t)ptr & (t == KCS_F32 ? 15u : 7u)) == 0;
 }
 
-int kcs_osl_ratio_ex(const kcs_geometry_t* g, int subset, int n_frames, const float* frame_dt,
+static int osl_ratio(const kcs_geometry_t* g, int subset, int n_frames, const float* frame_dt,
                      float kappa, const void* counts, int counts_type, const float* randoms,
                      int randoms_layout, const float* bin_factor, const void* x, int x_type,
-                     const float* x_scale, void* rho, void* stream) {
-  clear_error();
+                     const float* x_scale, void* rho, int rho_q, void* stream) {
   int st = check_geom(g, subset, n_frames);
   if (st) return st;
   KCS_REQUIRE(subset >= 0, "the ratio needs a subset index >= 0");
@@ -1028,6 +1039,7 @@ int kcs_osl_ratio_ex(const kcs_geometry_t* g, int subset, int n_frames, const fl
   p.x = x;
   p.xscale = reinterpret_cast<const float4*>(x_scale);
   p.yout = rho;
+  p.yq = rho_q;
   p.counts = counts;
   p.randoms = reinterpret_cast<const float4*>(randoms);
   p.randoms_layout = randoms_layout;
@@ -1082,14 +1094,13 @@ int kcs_osl_ratio(const kcs_geometry_t* g, int subset, int n_frames, const float
                   float kappa, const float* counts, const float* randoms, int randoms_layout,
                   const float* bin_factor, const float* x, float* rho, void* stream) {
   return kcs_osl_ratio_ex(g, subset, n_frames, frame_dt, kappa, counts, KCS_F32, randoms,
-                          randoms_layout, bin_factor, x, KCS_F32, nullptr, rho, stream);
+                          randoms_layout, bin_factor, x, KCS_F32, nullptr, rho, n_frames, stream);
 }
 
-int kcs_osl_backproject_ex(const kcs_geometry_t* g, int subset, int n_frames,
+static int osl_backproject(const kcs_geometry_t* g, int subset, int n_frames,
                            const float* frame_dt, float kappa, const float* bin_factor,
-                           const void* rho, const float* F_model, float beta_kp, float sigma2,
-                           void* x, int x_type, const float* x_scale, void* stream) {
-  clear_error();
+                           const void* rho, int rho_q, const float* F_model, float beta_kp,
+                           float sigma2, void* x, int x_type, const float* x_scale, void* stream) {
   int st = check_geom(g, subset, n_frames);
   if (st) return st;
   KCS_REQUIRE(subset >= 0, "the OSL update needs a subset index >= 0");
@@ -1103,6 +1114,7 @@ int kcs_osl_backproject_ex(const kcs_geometry_t* g, int subset, int n_frames,
   q.x = x;
   q.xscale = reinterpret_cast<const float4*>(x_scale);
   q.y = rho;
+  q.yq = rho_q;
   q.xout = x;
   q.bin_factor = bin_factor;
   q.dt = reinterpret_cast<const float4*>(frame_dt);
@@ -1115,12 +1127,46 @@ int kcs_osl_backproject_ex(const kcs_geometry_t* g, int subset, int n_frames,
   return KCS_OK;
 }
 
+int kcs_osl_rho_frames(int n_frames, int x_type) {
+  if (n_frames <= 0 || n_frames % 4) return n_frames;
+  return 4 * rho_pitch(n_frames / 4, x_type);
+}
+
+static int check_rho_frames(int n_frames, int rho_frames) {
+  KCS_REQUIRE(rho_frames >= n_frames && rho_frames % 4 == 0 && rho_frames <= 4 * 64,
+              "rho_frames %d must be a multiple of 4 in [n_frames=%d, 256]", rho_frames, n_frames);
+  return KCS_OK;
+}
+
+int kcs_osl_ratio_ex(const kcs_geometry_t* g, int subset, int n_frames, const float* frame_dt,
+                     float kappa, const void* counts, int counts_type, const float* randoms,
+                     int randoms_layout, const float* bin_factor, const void* x, int x_type,
+                     const float* x_scale, void* rho, int rho_frames, void* stream) {
+  clear_error();
+  const int st = check_rho_frames(n_frames, rho_frames);
+  if (st) return st;
+  return osl_ratio(g, subset, n_frames, frame_dt, kappa, counts, counts_type, randoms,
+                   randoms_layout, bin_factor, x, x_type, x_scale, rho, rho_frames / 4, stream);
+}
+
+int kcs_osl_backproject_ex(const kcs_geometry_t* g, int subset, int n_frames,
+                           const float* frame_dt, float kappa, const float* bin_factor,
+                           const void* rho, int rho_frames, const float* F_model, float beta_kp,
+                           float sigma2, void* x, int x_type, const float* x_scale,
+                           void* stream) {
+  clear_error();
+  const int st = check_rho_frames(n_frames, rho_frames);
+  if (st) return st;
+  return osl_backproject(g, subset, n_frames, frame_dt, kappa, bin_factor, rho, rho_frames / 4,
+                         F_model, beta_kp, sigma2, x, x_type, x_scale, stream);
+}
+
 int kcs_osl_backproject(const kcs_geometry_t* g, int subset, int n_frames, const float* frame_dt,
                         float kappa, const float* bin_factor, const float* rho,
                         const float* F_model, float beta_kp, float sigma2, float* x,
                         void* stream) {
-  return kcs_osl_backproject_ex(g, subset, n_frames, frame_dt, kappa, bin_factor, rho, F_model,
-                                beta_kp, sigma2, x, KCS_F32, nullptr, stream);
+  return kcs_osl_backproject_ex(g, subset, n_frames, frame_dt, kappa, bin_factor, rho, n_frames,
+                                F_model, beta_kp, sigma2, x, KCS_F32, nullptr, stream);
 }
 
 int kcs_osl_update_ex(const kcs_geometry_t* g, int subset, int n_frames, const float* frame_dt,
@@ -1133,11 +1179,12 @@ int kcs_osl_update_ex(const kcs_geometry_t* g, int subset, int n_frames, const f
   if (st) return st;
   KCS_REQUIRE(workspace && ws_bytes >= kcs_osl_workspace_size(g, n_frames),
               "workspace too small (%zu < %zu)", ws_bytes, kcs_osl_workspace_size(g, n_frames));
-  st = kcs_osl_ratio_ex(g, subset, n_frames, frame_dt, kappa, counts, counts_type, randoms,
-                        randoms_layout, bin_factor, x, x_type, x_scale, workspace, stream);
+  const int rq = rho_pitch(n_frames / 4, x_type);
+  st = osl_ratio(g, subset, n_frames, frame_dt, kappa, counts, counts_type, randoms,
+                 randoms_layout, bin_factor, x, x_type, x_scale, workspace, rq, stream);
   if (st) return st;
-  return kcs_osl_backproject_ex(g, subset, n_frames, frame_dt, kappa, bin_factor, workspace,
-                                F_model, beta_kp, sigma2, x, x_type, x_scale, stream);
+  return osl_backproject(g, subset, n_frames, frame_dt, kappa, bin_factor, workspace, rq,
+                         F_model, beta_kp, sigma2, x, x_type, x_scale, stream);
 }
 
 int kcs_osl_update(const kcs_geometry_t* g, int subset, int n_frames, const float* frame_dt,

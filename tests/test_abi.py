@@ -60,6 +60,9 @@ def test_workspace_sizes_without_gpu():
     from paper_1803_10045_b300._lib import lib
     assert lib.kcs_lm_workspace_size(10, 10, 2) >= 5 * 200 * 4
     assert lib.kcs_lm_workspace_size(0, 10, 2) == 0
+    # ratio row pitch: float rows padded to an odd number of 4-frame quads
+    assert [lib.kcs_osl_rho_frames(M, 0) for M in (4, 8, 12, 24, 32)] == [4, 12, 12, 28, 36]
+    assert [lib.kcs_osl_rho_frames(M, 1) for M in (4, 8, 24)] == [4, 8, 24]
 
 
 def test_empty_voxel_sets_need_no_buffers():

@@ -119,3 +119,35 @@ def test_loglik_matches_oracle(cuda_ok, randoms):
                    randoms=None if r is None else tt(r_m)).item()
     print(f"loglik gpu {got:.9e} oracle {ref:.9e} rel {abs(got / ref - 1):.2e}")
     assert abs(got / ref - 1) < 1e-5
+
+
+@pytest.mark.parametrize("M", [8, 12, 24])
+def test_split_ratio_pitch_equals_fused_update(cuda_ok, M):
+    """The two halves of the update at any ratio row pitch (dense, the padded
+    pitch the fused update keeps internally, a wider one) give the fused
+    update's image bit for bit, and the ratio frames agree bit for bit."""
+    import paper_1803_10045_b300 as K
+    nx, ny, nz, B, A, Sb = 37, 31, 2, 47, 36, 4
+    og = OP.Geometry(nx, ny, 2.0, B, A, 2.0, Sb)
+    rng = np.random.default_rng(M)
+    x_true = rng.uniform(0.5, 3.0, (nz, ny, nx, M))
+    dt = _f32(np.linspace(0.25, 3.0, M))
+    counts = rng.poisson(og.forward(x_true) * 3.0 * dt + 0.5).astype(float)
+    x0, F = _f32(rng.uniform(0.5, 3.0, x_true.shape)), _f32(x_true)
+    kg = K.Geometry(nx, ny, nz, 2.0, B, A, 2.0, Sb)
+    k = 1
+    fused = _t(x0)
+    K.osl_update(kg, k, fused, _t(dt), 3.0, _t(counts), F=_t(F), beta=2.0)
+    pitches = sorted({M, K.rho_frames(M), M + 8})
+    assert K.rho_frames(M) == (M + 4 if (M // 4) % 2 == 0 else M)
+    rhos = []
+    for P in pitches:
+        rho = torch.full(kg.sino_shape(P, k), float("nan"), device="cuda")
+        K.osl_ratio(kg, k, _t(x0), _t(dt), 3.0, _t(counts), out=rho)
+        xs = _t(x0)
+        K.osl_backproject(kg, k, xs, _t(dt), 3.0, rho, F=_t(F), beta=2.0)
+        assert torch.equal(xs, fused), P
+        rhos.append(rho[..., :M])
+    for r in rhos[1:]:
+        assert torch.equal(r, rhos[0])
+    assert torch.isnan(rho[..., M:]).all()     # padding frames are never written
