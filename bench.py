@@ -78,8 +78,8 @@ LM_FLOPS_PER_VOXEL_STEP = lm_flops_per_voxel_step(frames=S.WORKLOADS["pr2"].n_fr
 # the kernel's source file is unchanged (sha256 prefix); see profiles/.
 TRAFFIC = {
     "lm_step": {"bytes": 471.02e6 * 127 / 16, "src": "kinetics.cu", "sha": "fb69861231073d0e"},
-    "bwd_osl": {"bytes": 506.56e6 * 127 / 16, "src": "projector.cu", "sha": "7e72329affffd00c"},
-    "fwd_ratio": {"bytes": 254.37e6 * 127 / 16, "src": "projector.cu", "sha": "7e72329affffd00c"},
+    "bwd_osl": {"bytes": 509.16e6 * 127 / 16, "src": "projector.cu", "sha": "f126ccf36c7cd7b0"},
+    "fwd_ratio": {"bytes": 255.66e6 * 127 / 16, "src": "projector.cu", "sha": "f126ccf36c7cd7b0"},
 }
 
 
