@@ -59,14 +59,13 @@ FP32_LANES_PER_SM, N_SM = 128, 148
 def lm_flops_per_voxel_step(frames=24, n_lm=10):
     """Nominal float32 flops (FMA = 2) of one MAP-LM voxel-step: one model +
     Jacobian evaluation at the trial point (the current point's normal
-    equations are kept from the previous step): per frame the Hermite
-    interpolants of A, B, A', B' (16 FMA), the model and its 4 derivatives
-    (~10 flop), the residual with its compensated square sum (~6) and the
-    normal equations (15 FMA): ~80 flop; ~30 for the interpolation basis, ~100
-    for the 4x4 solve, ~384 for the Huber terms of the current and trial
-    points; plus the evaluation at the start point amortised over the n_lm
-    steps of a fit."""
-    return round((80 * frames + 30) * (1 + 1 / n_lm) + 100 + 384)
+    equations are kept from the previous step): per frame the cell cubics of
+    A, B and their slopes (10 FMA), the model and its 4 derivatives (~12
+    flop), the residual with its compensated square sum (~6) and the normal
+    equations (15 FMA): ~68 flop; ~5 for the cell coordinate, ~100 for the 4x4
+    solve, ~384 for the Huber terms of the current and trial points; plus the
+    evaluation at the start point amortised over the n_lm steps of a fit."""
+    return round((68 * frames + 5) * (1 + 1 / n_lm) + 100 + 384)
 
 
 LM_FLOPS_PER_VOXEL_STEP = lm_flops_per_voxel_step(frames=S.WORKLOADS["pr2"].n_frames)

@@ -203,11 +203,13 @@ int kcs_init_image_ex(const kcs_geometry_t* g, int n_frames, const float* frame_
  *   F_m = (1/dt_m) int_{frame m} [(1 - Vb) C_T + Vb Cp] dt,
  * evaluated analytically (Sec. II-C).  With a fixed the model is linear in
  * K1, k3, Vb: F_m = (1 - Vb) K1 (A_m(a) + k3 B_m(a)) + Vb cp_m.  This call
- * tabulates A_m, B_m and their first and second a-derivatives once, in
- * float64 on the device, on a grid of a (spacing 1/512 per minute), from the
- * exact interval-by-interval convolution (per interval e^{-aD} times a power
- * series in a with non-negative input-moment coefficients); evaluations
- * interpolate that table (cubic Hermite, ~1e-8 of each frame's range).
+ * tabulates A_m, B_m and their a-derivatives once, in float64 on the device,
+ * at the nodes of a grid of a (spacing 1/512 per minute), from the exact
+ * interval-by-interval convolution (per interval e^{-aD} times a power series
+ * in a with non-negative input-moment coefficients), and keeps per grid cell
+ * the coefficients of the cubic Hermite interpolants; evaluations read one
+ * cell per frame (values within ~2e-7 of each frame's range, slopes within
+ * ~5e-6 of the largest slope).
  * t_start, t_end: host arrays of n_frames frame limits (ordered, no overlap;
  * gaps allowed); feng: host {A1, A2, A3, l1, l2, l3}.  Valid for
  * 0 <= k2 + k3 <= 3.75 per minute (the LM box reaches 3).  Synchronous. */

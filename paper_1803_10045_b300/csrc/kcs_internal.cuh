@@ -102,22 +102,26 @@ inline size_t align256(size_t n) { return (n + 255) & ~size_t(255); }
 // PER_UNIT nodes per unit, 0 <= a <= A_MAX) once per frame schedule, from the
 // input moments of every propagation interval (power series in a with
 // non-negative coefficients, no cancellation near a -> 0 or a -> an input
-// exponent); a voxel then evaluates cubic Hermite interpolants in a: per
-// frame two 16-byte table reads and a few fused multiply-adds.  Table layout
-// [frame][node] (A, A', B, B'), so the lanes of a warp (voxels with similar a)
-// read neighbouring entries.
+// exponent).  Each grid cell holds, per frame, the coefficients of the cubic
+// Hermite interpolants of A and B in the cell's local coordinate (formed in
+// float64, rounded once): a voxel reads one aligned 32-byte entry per frame and
+// evaluates A, B and their derivatives with a few fused multiply-adds.  Table
+// layout [frame][cell], so the lanes of a warp (voxels with similar a) read
+// neighbouring entries.
 constexpr int NB = 128;                 // base terms of the input moments (float64)
 constexpr double DT_MAX = 5.0;          // longest propagation interval (min)
 constexpr int NODES_PER_UNIT = 512;     // grid spacing h = 1/512 in a (1/min)
 constexpr double A_MAX = 3.75;          // tabulated range of a (the fit's box has a <= 3)
 constexpr int N_NODES = (int)(A_MAX * NODES_PER_UNIT) + 2;
+constexpr int N_CELLS = N_NODES - 1;
 
 // Channel numbering of the float64 base series.
 enum { CH_M1 = 0, CH_G, CH_M2, CH_H, CH_M3, CH_D1, CH_GP, CH_D2, CH_HP, CH_D3 };
 
 struct KinDev {
-  const float4* node;   // [M][N_NODES] (A, dA/da, B, dB/da) at a = n / NODES_PER_UNIT
-  const float2* node2;  // [M][N_NODES] (d2A/da2, d2B/da2)
+  // [M][N_CELLS][2]: cubic coefficients (c0, c1, c2, c3) of A, then of B, on
+  // cell c in s = a NODES_PER_UNIT - c:  A = c0 + s c1 + s^2 c2 + s^3 c3
+  const float4* cell;
   const float* fr_cp;   // [M] frame average of Cp
   int M;
 };
@@ -128,13 +132,12 @@ struct kcs_kinetics {
   int M;
   int n_iv;
   int device;
-  float4* d_node;
-  float2* d_node2;
+  float4* d_cell;
   float* d_fr_cp;
   int* d_iv_code;
   double* d_tmp;   // per-interval doubles used while tabulating
   double* d_base;  // [n_iv][NB][10] float64 base series
-  kcs::KinDev dev() const { return kcs::KinDev{d_node, d_node2, d_fr_cp, M}; }
+  kcs::KinDev dev() const { return kcs::KinDev{d_cell, d_fr_cp, M}; }
 };
 
 namespace kcs {

@@ -157,34 +157,46 @@ __device__ void frame_averages(double a, const double* base, const double* iv_dt
   }
 }
 
-// Node tables at a = n / NODES_PER_UNIT: (A, A', B, B') and the second
-// derivatives (A'', B'') by a central difference of the float64 first
-// derivatives with step 1e-4 (truncation ~1e-6 relative, far below the float32
-// table precision).  One thread per node.
-constexpr double NODE_FD_STEP = 1e-4;
+// Float64 node values (A, A', B, B') at a = n / NODES_PER_UNIT, [frame][node][4].
+// One thread per node.
 __global__ void k_node_table(const double* base, const double* iv_dt, const int* iv_code,
-                             int n_iv, const double* fdt, int M, int nn, float4* node,
-                             float2* node2) {
+                             int n_iv, const double* fdt, int nn, double* node) {
   const int n = blockIdx.x * blockDim.x + threadIdx.x;
   if (n >= nn) return;
   const double a = (double)n / NODES_PER_UNIT;
-  double dp[2 * 32];                               // A', B' at a + step, per frame
-  frame_averages(a + NODE_FD_STEP, base, iv_dt, iv_code, n_iv, fdt,
-                 [&](int m, double, double Ap, double, double Bp) {
-                   dp[2 * m] = Ap;
-                   dp[2 * m + 1] = Bp;
-                 });
-  frame_averages(a - NODE_FD_STEP, base, iv_dt, iv_code, n_iv, fdt,
-                 [&](int m, double, double Ap, double, double Bp) {
-                   const double s = 0.5 / NODE_FD_STEP;
-                   node2[(size_t)m * nn + n] =
-                       make_float2((float)((dp[2 * m] - Ap) * s), (float)((dp[2 * m + 1] - Bp) * s));
-                 });
   frame_averages(a, base, iv_dt, iv_code, n_iv, fdt,
                  [&](int m, double A, double Ap, double B, double Bp) {
-                   node[(size_t)m * nn + n] = make_float4((float)A, (float)Ap, (float)B, (float)Bp);
+                   double* o = node + ((size_t)m * nn + n) * 4;
+                   o[0] = A; o[1] = Ap; o[2] = B; o[3] = Bp;
                  });
-  (void)M;
+}
+
+// Cubic Hermite coefficients per cell and frame, in float64 from the node
+// values and slopes (h = cell width): on s in [0, 1],
+//   c0 = f(0), c1 = h f'(0), c2 = 3 (f(1) - f(0)) - h (2 f'(0) + f'(1)),
+//   c3 = 2 (f(0) - f(1)) + h (f'(0) + f'(1)),
+// then rounded once to float.  The derivative comes from the same cubic
+// (c1 + 2 s c2 + 3 s^2 c3) / h: its coefficients carry the differences in
+// float64, so nothing cancels in float32 (truncation ~4e-6 of the largest
+// slope at h = 1/512).
+__global__ void k_cell_table(const double* node, int M, int nn, float4* cell) {
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  const int nc = nn - 1;
+  if (e >= M * nc) return;
+  const int m = e / nc, c = e - m * nc;
+  const double h = 1.0 / NODES_PER_UNIT;
+  const double* n0 = node + ((size_t)m * nn + c) * 4;
+  const double* n1 = n0 + 4;
+  float co[2][4];
+  for (int f = 0; f < 2; ++f) {
+    const double f0 = n0[2 * f], d0 = n0[2 * f + 1], f1 = n1[2 * f], d1 = n1[2 * f + 1];
+    co[f][0] = (float)f0;
+    co[f][1] = (float)(h * d0);
+    co[f][2] = (float)(3.0 * (f1 - f0) - h * (2.0 * d0 + d1));
+    co[f][3] = (float)(2.0 * (f0 - f1) + h * (d0 + d1));
+  }
+  cell[2 * (size_t)e] = make_float4(co[0][0], co[0][1], co[0][2], co[0][3]);
+  cell[2 * (size_t)e + 1] = make_float4(co[1][0], co[1][1], co[1][2], co[1][3]);
 }
 
 __global__ void k_frame_tables(const double* m0, const int* code, int n_iv, const double* fdt,
@@ -203,51 +215,44 @@ __global__ void k_frame_tables(const double* m0, const int* code, int n_iv, cons
 // S = A + k3 B:  F = w K1 S + Vb cp,  dF/dK1 = w S,  dF/dk2 = w K1 (A' + k3 B'),
 // dF/dk3 = w K1 (A' + B + k3 B') = -w K1 k2 B'  (A' + B = -a B' from
 // I' = Cp - a I: a single term, exactly 0 at k2 = 0, instead of a cancelling
-// difference),  dF/dVb = cp - K1 S.  A, B are cubic Hermite interpolants of
-// the float64 node table (values and first derivatives at the two nodes around
-// a), A', B' those of the first and second derivatives.
-template <int VPT, bool JAC, class Sink>
+// difference),  dF/dVb = cp - K1 S.  A, B are the per-cell cubics of the
+// table (cubic Hermite interpolants of the float64 node values and slopes),
+// A', B' their derivatives.
+template <int VPT, bool JAC, int MU = 1, class Sink>
 __device__ __forceinline__ void eval_model(const KinDev& kd, const float (&K1)[VPT],
                                            const float (&k2)[VPT], const float (&k3)[VPT],
                                            const float (&Vb)[VPT], Sink& sink) {
-  constexpr float h = 1.0f / NODES_PER_UNIT;
   int j[VPT];
-  float b00[VPT], b10[VPT], b01[VPT], b11[VPT];   // Hermite basis (h folded in)
+  float t[VPT], d2[VPT], d3[VPT];
 #pragma unroll
   for (int v = 0; v < VPT; ++v) {
     const float a = fmaxf(k2[v] + k3[v], 0.f);
     const float u = a * (float)NODES_PER_UNIT;
-    j[v] = min((int)u, N_NODES - 2);                // a beyond A_MAX extrapolates
-    const float t = u - (float)j[v];
-    const float t2 = t * t, t3 = t2 * t;
-    b00[v] = fmaf(2.f, t3, fmaf(-3.f, t2, 1.f));
-    b10[v] = (t3 - 2.f * t2 + t) * h;
-    b01[v] = fmaf(-2.f, t3, 3.f * t2);
-    b11[v] = (t3 - t2) * h;
+    j[v] = min((int)u, N_CELLS - 1);                // a beyond A_MAX extrapolates
+    t[v] = u - (float)j[v];
+    d2[v] = 2.f * t[v];
+    d3[v] = 3.f * t[v] * t[v];
   }
+#pragma unroll MU
   for (int m = 0; m < kd.M; ++m) {
     const float cp = __ldg(kd.fr_cp + m);
-    const float4* row = kd.node + (size_t)m * N_NODES;
-    const float2* row2 = kd.node2 + (size_t)m * N_NODES;
+    const float4* row = kd.cell + (size_t)m * N_CELLS * 2;
 #pragma unroll
     for (int v = 0; v < VPT; ++v) {
-      const float4 c0 = __ldg(row + j[v]);
-      const float4 c1 = __ldg(row + j[v] + 1);
-      const float A = fmaf(b00[v], c0.x, fmaf(b10[v], c0.y, fmaf(b01[v], c1.x, b11[v] * c1.y)));
-      const float B = fmaf(b00[v], c0.z, fmaf(b10[v], c0.w, fmaf(b01[v], c1.z, b11[v] * c1.w)));
+      const float4 ca = __ldg(row + 2 * j[v]);
+      const float4 cb = __ldg(row + 2 * j[v] + 1);
+      const float A = fmaf(t[v], fmaf(t[v], fmaf(t[v], ca.w, ca.z), ca.y), ca.x);
+      const float B = fmaf(t[v], fmaf(t[v], fmaf(t[v], cb.w, cb.z), cb.y), cb.x);
       const float S = fmaf(k3[v], B, A);
       const float T = K1[v] * S;
       const float F = fmaf(Vb[v], cp - T, T);       // (1 - Vb) T + Vb cp
       if (JAC) {
-        // the derivatives interpolate the tabulated (A', A'') and (B', B''):
-        // differentiating the value interpolant instead would subtract two
-        // rounded float32 node values (relative errors up to 1e-3)
-        const float2 e0 = __ldg(row2 + j[v]);
-        const float2 e1 = __ldg(row2 + j[v] + 1);
-        const float Ap = fmaf(b00[v], c0.y, fmaf(b10[v], e0.x, fmaf(b01[v], c1.y, b11[v] * e1.x)));
-        const float Bp = fmaf(b00[v], c0.w, fmaf(b10[v], e0.y, fmaf(b01[v], c1.w, b11[v] * e1.y)));
+        // h A' and h B' (h = 1 / NODES_PER_UNIT, a power of two: exact scaling)
+        const float Aph = fmaf(d3[v], ca.w, fmaf(d2[v], ca.z, ca.y));
+        const float Bph = fmaf(d3[v], cb.w, fmaf(d2[v], cb.z, cb.y));
         const float w = 1.f - Vb[v];
-        sink(v, m, F, w * S, w * K1[v] * fmaf(k3[v], Bp, Ap), -w * K1[v] * k2[v] * Bp, cp - T);
+        const float wK = w * K1[v] * (float)NODES_PER_UNIT;
+        sink(v, m, F, w * S, wK * fmaf(k3[v], Bph, Aph), -wK * k2[v] * Bph, cp - T);
       } else {
         sink(v, m, F, 0.f, 0.f, 0.f, 0.f);
       }
@@ -257,6 +262,11 @@ __device__ __forceinline__ void eval_model(const KinDev& kd, const float (&K1)[V
 
 // ---------------------------------------------------------------- tac_eval
 constexpr int TAC_THREADS = 128;
+// frames per trip of the model loop in k_tac_eval (one voxel per thread: two
+// frames' table reads in flight)
+#ifndef KCS_TAC_UNROLL
+#define KCS_TAC_UNROLL 2
+#endif
 
 struct TacSink {
   float* sF;   // shared row of this voxel: M floats
@@ -289,7 +299,7 @@ __global__ void __launch_bounds__(TAC_THREADS) k_tac_eval(KinDev kd, long long n
     const float K1[1] = {params[v]}, k2[1] = {params[n_vox + v]}, k3[1] = {params[2 * n_vox + v]},
                 Vb[1] = {params[3 * n_vox + v]};
     TacSink sink{sF + threadIdx.x * ldF, JAC ? sJ + threadIdx.x * ldJ : nullptr};
-    eval_model<1, JAC>(kd, K1, k2, k3, Vb, sink);
+    eval_model<1, JAC, KCS_TAC_UNROLL>(kd, K1, k2, k3, Vb, sink);
   }
   __syncthreads();
   for (long long e = threadIdx.x; e < nv * M; e += TAC_THREADS) {
@@ -811,14 +821,16 @@ int kcs_create_kinetics(kcs_kinetics_t** out, int n_frames, const double* t_star
   gauss_legendre(NGL, gx, gw);
   cudaStream_t s = as_stream(stream);
   const size_t nd = 2 * (size_t)n_iv + 2 * NGL + n_frames + n_iv;
-  bool ok = cudaMalloc(&k->d_node, sizeof(float4) * (size_t)n_frames * N_NODES) == cudaSuccess;
-  ok = ok && cudaMalloc(&k->d_node2, sizeof(float2) * (size_t)n_frames * N_NODES) == cudaSuccess;
+  double* d_node64 = nullptr;   // float64 node values, freed once the cell table exists
+  bool ok = cudaMalloc(&k->d_cell, sizeof(float4) * 2 * (size_t)n_frames * N_CELLS) == cudaSuccess;
+  ok = ok && cudaMalloc(&d_node64, sizeof(double) * 4 * (size_t)n_frames * N_NODES) == cudaSuccess;
   ok = ok && cudaMalloc(&k->d_base, sizeof(double) * (size_t)n_iv * NB * 10) == cudaSuccess;
   ok = ok && cudaMalloc(&k->d_iv_code, sizeof(int) * n_iv) == cudaSuccess;
   ok = ok && cudaMalloc(&k->d_fr_cp, sizeof(float) * n_frames) == cudaSuccess;
   ok = ok && cudaMalloc(&k->d_tmp, sizeof(double) * nd) == cudaSuccess;
   if (!ok) {
     set_error("cudaMalloc failed for kinetics tables");
+    cudaFree(d_node64);
     kcs_destroy_kinetics(k);
     return KCS_ERR_OOM;
   }
@@ -844,14 +856,23 @@ int kcs_create_kinetics(kcs_kinetics_t** out, int n_frames, const double* t_star
   k_tabulate<<<n_iv, NB, 0, s>>>(ta);
   KCS_LAUNCHED();
   k_node_table<<<(N_NODES + 127) / 128, 128, 0, s>>>(k->d_base, ta.iv_dt, k->d_iv_code, n_iv,
-                                                       k->d_tmp + 2 * n_iv + 2 * NGL, n_frames,
-                                                       N_NODES, k->d_node, k->d_node2);
+                                                       k->d_tmp + 2 * n_iv + 2 * NGL, N_NODES,
+                                                       d_node64);
+  KCS_LAUNCHED();
+  k_cell_table<<<(n_frames * N_CELLS + 127) / 128, 128, 0, s>>>(d_node64, n_frames, N_NODES,
+                                                                k->d_cell);
   KCS_LAUNCHED();
   k_frame_tables<<<1, 32, 0, s>>>(ta.m0, k->d_iv_code, n_iv, k->d_tmp + 2 * n_iv + 2 * NGL,
                                   n_frames, k->d_fr_cp);
   KCS_LAUNCHED();
-  // the host staging vectors die here: wait for the copies
-  KCS_CUDA(cudaStreamSynchronize(s));
+  // the host staging vectors die here: wait for the copies and the tables
+  const cudaError_t e = cudaStreamSynchronize(s);
+  cudaFree(d_node64);
+  if (e != cudaSuccess) {
+    set_error("kinetics tables: %s", cudaGetErrorString(e));
+    kcs_destroy_kinetics(k);
+    return KCS_ERR_CUDA;
+  }
   *out = k;
   return KCS_OK;
 }
@@ -859,8 +880,7 @@ int kcs_create_kinetics(kcs_kinetics_t** out, int n_frames, const double* t_star
 int kcs_destroy_kinetics(kcs_kinetics_t* k) {
   clear_error();
   if (!k) return KCS_OK;
-  cudaFree(k->d_node);
-  cudaFree(k->d_node2);
+  cudaFree(k->d_cell);
   cudaFree(k->d_base);
   cudaFree(k->d_iv_code);
   cudaFree(k->d_fr_cp);
