@@ -421,6 +421,11 @@ __global__ void k_huber_grad(int nx, int ny, int nz, const float* p, float delta
 #ifndef KCS_LM_CARVEOUT
 #define KCS_LM_CARVEOUT 50   // percent of the maximum shared memory per SM
 #endif
+// frames per trip of the model loop in the LM kernels (two frames' cell reads
+// in flight; 4 gains nothing, 80 registers for 6 blocks per SM lose 20 %)
+#ifndef KCS_LM_UNROLL
+#define KCS_LM_UNROLL 2
+#endif
 #ifndef KCS_LM_MINBLOCKS
 #define KCS_LM_MINBLOCKS 8
 #endif
@@ -658,7 +663,7 @@ __global__ void __launch_bounds__(LM_THREADS, KCS_LM_MINBLOCKS) k_lm_normal(LmAr
     ns.n[k] = Normal{0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
     ns.rr[k] = KSum{0.f, 0.f};
   }
-  eval_model<LM_VPT, true>(L.kd, K1, k2, k3, Vb, ns);
+  eval_model<LM_VPT, true, KCS_LM_UNROLL>(L.kd, K1, k2, k3, Vb, ns);
 #pragma unroll
   for (int k = 0; k < LM_VPT; ++k)
     if (act[k]) store_normal(L.ne_out, V, vv[k], ns.n[k], ns.rr[k]);
@@ -723,7 +728,7 @@ __global__ void __launch_bounds__(LM_THREADS, KCS_LM_MINBLOCKS) k_lm_step(LmArgs
     for (int k = 0; k < LM_VPT; ++k) {
       t1[k] = tr[k][0]; t2[k] = tr[k][1]; t3[k] = tr[k][2]; t4[k] = tr[k][3];
     }
-    eval_model<LM_VPT, true>(L.kd, t1, t2, t3, t4, ns);
+    eval_model<LM_VPT, true, KCS_LM_UNROLL>(L.kd, t1, t2, t3, t4, ns);
   }
 #pragma unroll
   for (int k = 0; k < LM_VPT; ++k) {
