@@ -356,6 +356,21 @@ int kcs_create_study(kcs_study_t** out, const kcs_study_desc_t* desc);
 int kcs_destroy_study(kcs_study_t* st);
 /* Run n_iter ICM iterations (asynchronous on stream). */
 int kcs_icm_iterate(kcs_study_t* st, int n_iter, void* stream);
+/* kcs_icm_iterate with host I/O for streaming a study through the GPU:
+ * before each iteration the counts are copied from counts_host (pinned host
+ * memory holding the study's counts in their layout and type; NULL: no
+ * copy) into the study's counts buffer, and after each iteration the maps are
+ * copied to params_host + k * params_host_stride floats (pinned host memory,
+ * [4][Z][ny][nx] per iteration; stride 0 overwrites one block, otherwise the
+ * stride is >= 4 x voxels; NULL: no copy).  The copies run on a private
+ * stream and overlap the compute: iteration k+1's counts arrive during
+ * iteration k's MAP-LM steps (which do not read the counts), iteration k's
+ * maps leave during iteration k+1's OSL pass (which does not touch them).
+ * Results equal kcs_icm_iterate's bit for bit.  Asynchronous: the caller's
+ * stream completes after the last copy; the host buffers must stay valid
+ * until then.  Host-issued (no graph replay). */
+int kcs_icm_iterate_host(kcs_study_t* st, int n_iter, const void* counts_host,
+                         float* params_host, size_t params_host_stride, void* stream);
 /* Replay the steady-state ICM iteration (prior on) from a CUDA graph recorded
  * at its first use (enable = 1), or issue every launch from the host (enable =
  * 0, the default; also releases a recorded graph).  Results are identical;

@@ -87,6 +87,7 @@ SIGNATURES = {
     "kcs_create_study": (i32, [pp, C.POINTER(StudyDesc)]),
     "kcs_destroy_study": (i32, [vp]),
     "kcs_icm_iterate": (i32, [vp, i32, vp]),
+    "kcs_icm_iterate_host": (i32, [vp, i32, vp, vp, sz, vp]),
     "kcs_study_iterations": (i32, [vp]),
     "kcs_study_set_iterations": (i32, [vp, i32]),
     "kcs_study_set_graph": (i32, [vp, i32]),

@@ -400,6 +400,38 @@ class Study:
     def iterate(self, n_iter=1):
         check(lib.kcs_icm_iterate(self.handle, int(n_iter), _stream()))
 
+    def iterate_host(self, n_iter, counts_host=None, params_host=None):
+        """n_iter ICM iterations streaming host data: the counts are copied in
+        from counts_host (pinned, the study's counts shape and dtype) before
+        every iteration and the maps copied out to params_host after every
+        iteration (pinned float32, [4][Z][ny][nx] overwritten each time, or
+        [n_iter][4][Z][ny][nx] for one set per iteration).  The copies overlap
+        the compute; results equal iterate's.  Asynchronous on the current
+        stream; keep the host tensors alive until it completes."""
+        g = self.geom
+        counts = self._keep[3]
+        pc = pp = None
+        stride = 0
+        if counts_host is not None:
+            if (counts_host.device.type != "cpu" or not counts_host.is_pinned()
+                    or counts_host.dtype != counts.dtype or counts_host.shape != counts.shape
+                    or not counts_host.is_contiguous()):
+                raise ValueError("counts_host must be pinned, contiguous and shaped like the counts")
+            pc = C.c_void_p(counts_host.data_ptr())
+        if params_host is not None:
+            shape = (4, g.nz, g.ny, g.nx)
+            if params_host.dim() == 5:
+                if tuple(params_host.shape) != (n_iter,) + shape:
+                    raise ValueError(f"params_host must be {(n_iter,) + shape} or {shape}")
+                stride = params_host[0].numel()
+            elif tuple(params_host.shape) != shape:
+                raise ValueError(f"params_host must be {shape} or {(n_iter,) + shape}")
+            if (params_host.device.type != "cpu" or not params_host.is_pinned()
+                    or params_host.dtype != torch.float32 or not params_host.is_contiguous()):
+                raise ValueError("params_host must be pinned, contiguous float32")
+            pp = C.c_void_p(params_host.data_ptr())
+        check(lib.kcs_icm_iterate_host(self.handle, int(n_iter), pc, pp, stride, _stream()))
+
     def loglik(self):
         """Poisson log-likelihood of the current image (0-d float64 tensor)."""
         g, kin, frame_dt, counts, x, params, F, randoms, bin_factor, workspace, x_scale = self._keep

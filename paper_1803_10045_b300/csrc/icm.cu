@@ -19,6 +19,9 @@ struct kcs_study {
   int device;
   cudaStream_t cap;       // private stream the steady-state iteration is captured on
   cudaGraphExec_t exec;   // one ICM iteration with the prior on (null until first use)
+  // host I/O of kcs_icm_iterate_host: a private copy stream and its events
+  cudaStream_t copy;
+  cudaEvent_t ev[4];      // OSL pass done, counts in, fit done, maps out
 };
 
 using namespace kcs;
@@ -31,11 +34,10 @@ namespace {
 float fit_beta_h(const kcs_study_desc_t& d) { return d.method == KCS_METHOD_KCS ? d.beta_h : 0.f; }
 int fit_nbhd(const kcs_study_desc_t& d) { return d.neighbourhood == 26 ? 26 : 8; }
 
-int issue_iteration(const kcs_study* st, bool prior, void* stream) {
+int issue_osl_pass(const kcs_study* st, bool prior, void* stream) {
   const kcs_study_desc_t& d = st->d;
   const kcs_geometry* g = d.geom;
-  const bool indirect = d.method == KCS_METHOD_INDIRECT;
-  if (indirect) prior = false;
+  if (d.method == KCS_METHOD_INDIRECT) prior = false;
   // host-side ranges (visible in Nsight timelines) around the issue of each phase
   nvtxRangePushA("kcs::osl_pass");
   for (int k = 0; k < g->S; ++k) {
@@ -50,13 +52,30 @@ int issue_iteration(const kcs_study* st, bool prior, void* stream) {
     }
   }
   nvtxRangePop();
-  if (indirect) return KCS_OK;
+  return KCS_OK;
+}
+
+// (b) the MAP-LM fit of the maps (and F <- F(params)); nothing for INDIRECT.
+int issue_fit(const kcs_study* st, void* stream) {
+  const kcs_study_desc_t& d = st->d;
+  const kcs_geometry* g = d.geom;
+  if (d.method == KCS_METHOD_INDIRECT) return KCS_OK;
   nvtxRangePushA("kcs::map_lm_fit");
   const int rc = kcs_map_lm_fit_nb(d.kin, g->nx, g->ny, g->nz, d.x, d.x_type, d.x_scale, d.params,
                            nullptr, d.n_lm, fit_beta_h(d), d.delta, fit_nbhd(d), d.F, d.workspace,
                            d.ws_bytes, stream);
   nvtxRangePop();
   return rc;
+}
+
+int issue_iteration(const kcs_study* st, bool prior, void* stream) {
+  const int rc = issue_osl_pass(st, prior, stream);
+  return rc ? rc : issue_fit(st, stream);
+}
+
+// The prior is on once an earlier iteration produced F (or the maps were given).
+bool prior_on(const kcs_study* st) {
+  return (st->iterations > 0 || st->d.params_given) && st->d.method != KCS_METHOD_INDIRECT;
 }
 
 // Record the steady-state iteration once into a CUDA graph.  Capture runs on a
@@ -119,6 +138,8 @@ int kcs_create_study(kcs_study_t** out, const kcs_study_desc_t* d) {
   st->device = d->geom->device;
   st->cap = nullptr;
   st->exec = nullptr;
+  st->copy = nullptr;
+  for (auto& e : st->ev) e = nullptr;
   *out = st;
   return KCS_OK;
 }
@@ -128,6 +149,9 @@ int kcs_destroy_study(kcs_study_t* st) {
   if (st) {
     release_graph(st);
     if (st->cap) cudaStreamDestroy(st->cap);
+    if (st->copy) cudaStreamDestroy(st->copy);
+    for (auto e : st->ev)
+      if (e) cudaEventDestroy(e);
   }
   delete st;
   return KCS_OK;
@@ -170,7 +194,7 @@ int kcs_icm_iterate(kcs_study_t* st, int n_iter, void* stream) {
   const long long V = (long long)d.geom->nz * d.geom->ny * d.geom->nx;
   cudaStream_t s = as_stream(stream);
   for (int it = 0; it < n_iter; ++it) {
-    const bool prior = (st->iterations > 0 || d.params_given) && d.method != KCS_METHOD_INDIRECT;
+    const bool prior = prior_on(st);
     if (prior && st->iterations == 0) {
       const int rc = launch_tac_eval(d.kin, V, d.params, d.F, nullptr, s);
       if (rc) return rc;
@@ -187,6 +211,74 @@ int kcs_icm_iterate(kcs_study_t* st, int n_iter, void* stream) {
     }
     st->iterations += 1;
   }
+  return KCS_OK;
+}
+
+int kcs_icm_iterate_host(kcs_study_t* st, int n_iter, const void* counts_host,
+                         float* params_host, size_t params_host_stride, void* stream) {
+  clear_error();
+  KCS_REQUIRE(st, "study is NULL");
+  KCS_REQUIRE(n_iter >= 0, "n_iter < 0");
+  const kcs_study_desc_t& d = st->d;
+  const kcs_geometry* g = d.geom;
+  const long long V = (long long)g->nz * g->ny * g->nx;
+  const size_t counts_bytes = (size_t)g->nz * g->A * g->B * d.n_frames *
+                              (d.counts_type == KCS_U16 ? 2 : 4);
+  const size_t maps_bytes = sizeof(float) * 4 * (size_t)V;
+  KCS_REQUIRE(params_host_stride == 0 || params_host_stride >= (size_t)4 * V,
+              "params_host_stride %zu is neither 0 nor >= 4 x voxels", params_host_stride);
+  if (n_iter == 0) return KCS_OK;
+  if (!st->copy) {
+    KCS_CUDA(cudaStreamCreateWithFlags(&st->copy, cudaStreamNonBlocking));
+    for (auto& e : st->ev) KCS_CUDA(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+  }
+  enum { OSL_DONE = 0, COUNTS_IN = 1, FIT_DONE = 2, MAPS_OUT = 3 };
+  cudaStream_t s = as_stream(stream), c = st->copy;
+  // everything already on the caller's stream (which may read the counts or
+  // the maps) precedes the first copy
+  KCS_CUDA(cudaEventRecord(st->ev[FIT_DONE], s));
+  KCS_CUDA(cudaStreamWaitEvent(c, st->ev[FIT_DONE], 0));
+  if (counts_host) {
+    KCS_CUDA(cudaMemcpyAsync(const_cast<void*>(d.counts), counts_host, counts_bytes,
+                             cudaMemcpyHostToDevice, c));
+  }
+  KCS_CUDA(cudaEventRecord(st->ev[COUNTS_IN], c));
+  KCS_CUDA(cudaEventRecord(st->ev[MAPS_OUT], c));
+  for (int it = 0; it < n_iter; ++it) {
+    const bool prior = prior_on(st);
+    KCS_CUDA(cudaStreamWaitEvent(s, st->ev[COUNTS_IN], 0));   // this iteration's counts
+    if (prior && st->iterations == 0) {
+      const int rc = launch_tac_eval(d.kin, V, d.params, d.F, nullptr, s);
+      if (rc) return rc;
+    }
+    int rc = issue_osl_pass(st, prior, s);
+    if (rc) return rc;
+    // the next iteration's counts arrive while this one fits the maps (the
+    // fit does not read the counts)
+    KCS_CUDA(cudaEventRecord(st->ev[OSL_DONE], s));
+    if (counts_host && it + 1 < n_iter) {
+      KCS_CUDA(cudaStreamWaitEvent(c, st->ev[OSL_DONE], 0));
+      KCS_CUDA(cudaMemcpyAsync(const_cast<void*>(d.counts), counts_host, counts_bytes,
+                               cudaMemcpyHostToDevice, c));
+      KCS_CUDA(cudaEventRecord(st->ev[COUNTS_IN], c));
+    }
+    // the previous iteration's maps have left before the fit overwrites them
+    KCS_CUDA(cudaStreamWaitEvent(s, st->ev[MAPS_OUT], 0));
+    rc = issue_fit(st, s);
+    if (rc) return rc;
+    st->iterations += 1;
+    // this iteration's maps leave during the next OSL pass (which does not
+    // touch them)
+    if (params_host) {
+      KCS_CUDA(cudaEventRecord(st->ev[FIT_DONE], s));
+      KCS_CUDA(cudaStreamWaitEvent(c, st->ev[FIT_DONE], 0));
+      KCS_CUDA(cudaMemcpyAsync(params_host + (size_t)it * params_host_stride, d.params,
+                               maps_bytes, cudaMemcpyDeviceToHost, c));
+      KCS_CUDA(cudaEventRecord(st->ev[MAPS_OUT], c));
+    }
+  }
+  // the caller's stream completes with the last copy
+  KCS_CUDA(cudaStreamWaitEvent(s, st->ev[MAPS_OUT], 0));
   return KCS_OK;
 }
 

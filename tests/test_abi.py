@@ -46,6 +46,7 @@ def test_invalid_arguments_are_rejected_on_the_host():
     assert lib.kcs_map_lm_fit(None, 4, 4, 1, None, None, None, 1, 0.1, 0.01, None, None, 0,
                               None) == 1
     assert lib.kcs_icm_iterate(None, 1, None) == 1
+    assert lib.kcs_icm_iterate_host(None, 1, None, None, 0, None) == 1
     assert lib.kcs_version() >= 1
 
 

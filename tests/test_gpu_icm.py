@@ -250,3 +250,45 @@ def test_degenerate_inputs_stay_finite(cuda_ok):
             assert torch.isfinite(t).all()
         hi = torch.tensor([2.0, 2.0, 1.0, 1.0], device="cuda")[:, None, None, None]
         assert (params >= 0).all() and (params <= hi).all()
+
+
+@pytest.mark.parametrize("counts_dtype", [torch.float32, torch.uint16])
+def test_streamed_host_io_equals_device_iterations(cuda_ok, counts_dtype):
+    """iterate_host (counts copied in before, maps copied out after every
+    iteration, overlapped with the compute) gives the device-only iterations'
+    image, maps and model TACs bit for bit, and each host map set equals the
+    device maps after that iteration."""
+    K, P, W, kg, kin = _setup()
+    dt = _t(_f32(P["dt"]))
+    kappa = float(np.float32(P["kappa"]))
+    counts = _t(P["counts"]).to(counts_dtype)
+    start = _t(np.broadcast_to(np.array(S.XI0)[:, None, None, None], (4, 1, W.ny, W.nx)))
+    n_it = 3
+
+    def fresh(cdev):
+        x = K.init_image(kg, dt, kappa, counts)
+        p = start.clone()
+        return x, p, K.Study(kg, kin, dt, kappa, cdev, x, p, n_lm=10, beta_kp=0.1, beta_h=0.1,
+                             delta=0.01)
+    xa, pa, a = fresh(counts)
+    per_iter = []
+    for _ in range(n_it):
+        a.iterate(1)
+        per_iter.append(pa.clone())
+    cdev = torch.zeros_like(counts)             # filled by the streamed copies only
+    xb, pb, b = fresh(cdev)
+    ch = torch.empty(counts.shape, dtype=counts.dtype, pin_memory=True)
+    ch.copy_(counts)
+    ph = torch.empty((n_it, 4, 1, W.ny, W.nx), dtype=torch.float32, pin_memory=True)
+    b.iterate_host(n_it, ch, ph)
+    torch.cuda.synchronize()
+    assert b.iterations == n_it
+    assert torch.equal(xa, xb) and torch.equal(pa, pb) and torch.equal(a.F, b.F)
+    assert torch.equal(cdev, counts)
+    for k in range(n_it):
+        assert torch.equal(ph[k], per_iter[k].cpu()), k
+    one = torch.empty((4, 1, W.ny, W.nx), dtype=torch.float32, pin_memory=True)
+    b.iterate_host(1, None, one)                # no counts copy; one overwritten block
+    a.iterate(1)
+    torch.cuda.synchronize()
+    assert torch.equal(one, pa.cpu()) and torch.equal(pa, pb)
