@@ -171,7 +171,53 @@ def oracle_sample(reps=1, seed=0):
     return json.loads(out.stdout.strip().splitlines()[-1])
 
 
-def _oracle_sample_inner(reps=1, seed=0):
+def _cpu_model():
+    try:
+        with open("/proc/cpuinfo") as f:
+            for line in f:
+                if line.startswith("model name"):
+                    return line.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    return "unknown"
+
+
+def oracle_sample_all_cores(max_procs=64, seed=0):
+    """The same oracle sample on every host core at once: one single-threaded
+    process per core (planes are independent), each timing its own sample
+    after a common start instant; the ICM rate of all cores together is the
+    per-core rate under that load times the number of processes."""
+    n = max(1, min(max_procs, len(os.sched_getaffinity(0))))
+    try:                                          # ~0.3 GB per process: stay in a quarter
+        with open("/proc/meminfo") as f:          # of the available host memory
+            avail_gb = next(int(l.split()[1]) for l in f if l.startswith("MemAvailable")) / 2**20
+        n = max(1, min(n, int(avail_gb / 4 / 0.3)))
+    except (OSError, StopIteration, ValueError):
+        pass
+    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1",
+               CUDA_VISIBLE_DEVICES="")
+    start_at = time.time() + 10.0 + 0.05 * n      # after every process has set up
+    code = ("import json, sys; sys.path.insert(0, {root!r}); import bench; "
+            "print(json.dumps(bench._oracle_sample_inner(1, {seed}, {start})))")
+    procs = [subprocess.Popen([sys.executable, "-c", code.format(root=ROOT, seed=seed + i,
+                                                                  start=start_at)],
+                              env=env, stdout=subprocess.PIPE, stderr=subprocess.DEVNULL,
+                              text=True) for i in range(n)]
+    vals = []
+    for p in procs:
+        out, _ = p.communicate()
+        if p.returncode == 0:
+            vals.append(json.loads(out.strip().splitlines()[-1]))
+    if not vals:
+        return None
+    per_core = statistics.median(v["value"] for v in vals)
+    return {"value": per_core * len(vals), "unit": "iter/s", "cores": len(vals),
+            "kind": "oracle", "cpu": _cpu_model(), "nproc": os.cpu_count(),
+            "sample": f"the 1-thread sample run concurrently in {len(vals)} processes, one "
+                      f"plane each; median per-process rate {per_core:.3g} iter/s x {len(vals)}"}
+
+
+def _oracle_sample_inner(reps=1, seed=0, start_at=None):
     from oracle import lm as OL
     from oracle import osl as OO
     from oracle import projector as OP
@@ -190,6 +236,8 @@ def _oracle_sample_inner(reps=1, seed=0):
     lam = np.full((1, 64, 64), 1e-2)
     t_osl, t_lm = [], []
     og.P(k)                                    # system matrix of the subset (setup)
+    if start_at is not None:                   # common start of concurrent samples
+        time.sleep(max(0.0, start_at - time.time()))
     for _ in range(reps):
         t0 = time.perf_counter()
         OO.osl_update(og, x, k, counts_k, 1.0, dt, F=F, beta=beta_kp_for(1.0))
@@ -430,6 +478,8 @@ def run_ours(args):
     }
     if not args.no_cpu_baseline:
         out["cpu_baseline"] = oracle_sample()
+        out["cpu_baseline"]["cpu"] = _cpu_model()
+        out["cpu_baseline"]["all_cores"] = oracle_sample_all_cores()
     print(json.dumps(out))
     if dist:
         dist.destroy_process_group()
