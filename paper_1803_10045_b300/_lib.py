@@ -23,7 +23,7 @@ class KcsError(RuntimeError):
 def _load():
     if not os.path.exists(LIB_PATH):
         raise ImportError(
-            f"{LIB_PATH} is missing: build it with `python -m paper_1803_10045_b300.build` "
+            f"{LIB_PATH} is missing: build it with `python paper_1803_10045_b300/build.py` "
             "(nvcc, sm_103a). There is no CPU fallback.")
     return C.CDLL(LIB_PATH)
 
