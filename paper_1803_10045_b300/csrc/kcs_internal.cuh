@@ -94,6 +94,21 @@ inline const int* subset_dev(const kcs_geometry* g, int k) {
 }
 inline size_t align256(size_t n) { return (n + 255) & ~size_t(255); }
 
+// Division by a runtime divisor d >= 2 as one multiply-high.  With
+// mul = ceil(2^32 / d) = (2^32 + e) / d, 0 <= e < d, the product n mul / 2^32
+// equals n / d + n e / (d 2^32); for n (d - 1) < 2^32 the second term is below
+// 1 / d, which cannot carry the fraction of n / d past the next integer, so
+// __umulhi(n, mul) = floor(n / d) exactly.  The 64-bit form (mul = ceil(2^64 /
+// d), __umul64hi) is exact for n (d - 1) < 2^64; d = 1 is encoded as mul = 0.
+inline unsigned div_magic32(unsigned d) { return (unsigned)((0x100000000ull + d - 1) / d); }
+inline unsigned long long div_magic64(unsigned long long d) {
+  return d < 2 ? 0ull
+               : (unsigned long long)((((unsigned __int128)1 << 64) + d - 1) / d);
+}
+__device__ __forceinline__ unsigned long long div64(unsigned long long n, unsigned long long mul) {
+  return mul ? __umul64hi(n, mul) : n;
+}
+
 // ------------------------------------------------------------ kinetics
 // The frame-integrated model is linear in K1, k3 and Vb once a = k2 + k3 is
 // fixed:  F_m = (1 - Vb) K1 (A_m(a) + k3 B_m(a)) + Vb cp_m,  with A_m, B_m the
@@ -124,6 +139,7 @@ struct KinDev {
   const float4* cell;
   const float* fr_cp;   // [M] frame average of Cp
   int M;
+  unsigned div_m, div_4m;   // div_magic32(M), div_magic32(4 M)
 };
 
 }  // namespace kcs
@@ -137,7 +153,10 @@ struct kcs_kinetics {
   int* d_iv_code;
   double* d_tmp;   // per-interval doubles used while tabulating
   double* d_base;  // [n_iv][NB][10] float64 base series
-  kcs::KinDev dev() const { return kcs::KinDev{d_cell, d_fr_cp, M}; }
+  kcs::KinDev dev() const {
+    return kcs::KinDev{d_cell, d_fr_cp, M, kcs::div_magic32((unsigned)M),
+                       kcs::div_magic32(4u * (unsigned)M)};
+  }
 };
 
 namespace kcs {

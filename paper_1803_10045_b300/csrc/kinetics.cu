@@ -358,8 +358,8 @@ __global__ void __launch_bounds__(TAC_THREADS) k_tac_vjp(KinDev kd, long long n_
   const long long v0 = (long long)blockIdx.x * TAC_THREADS;
   const long long v = v0 + threadIdx.x;
   const long long nv = min((long long)TAC_THREADS, n_vox - v0);
-  for (long long e = threadIdx.x; e < nv * M; e += TAC_THREADS) {
-    const long long r = e / M, m = e - r * M;
+  for (int e = threadIdx.x; e < (int)nv * M; e += TAC_THREADS) {
+    const int r = (int)__umulhi((unsigned)e, kd.div_m), m = e - r * M;
     sg[r * ld + m] = gF[v0 * M + e];
   }
   __syncthreads();
@@ -452,7 +452,17 @@ struct LmArgs {
   int nb3d;              // Huber neighbourhood: 0 in-plane 3x3, 1 the 3x3x3 cube
   const float* ne_in;    // [16][V] normal equations at the current point
   float* ne_out;         // [16][V] normal equations at the returned point
+  unsigned long long div_nx, div_nxy;   // div_magic64(nx), div_magic64(nx ny)
 };
+
+// Column, row and plane of voxel v.
+__device__ __forceinline__ void voxel_ijz(const LmArgs& L, long long v, int& i, int& j, int& z) {
+  const unsigned long long row = div64((unsigned long long)v, L.div_nx);   // v / nx
+  const unsigned long long pl = div64((unsigned long long)v, L.div_nxy);   // v / (nx ny)
+  i = (int)((unsigned long long)v - row * (unsigned long long)L.nx);
+  j = (int)(row - pl * (unsigned long long)L.ny);
+  z = (int)pl;
+}
 
 // Compensated (Kahan) float32 sum: the value is s - c.
 struct KSum {
@@ -628,10 +638,11 @@ __device__ __forceinline__ void stage_tacs(const LmArgs& L, float* xs_all, long 
                                            long long nv) {
   const int M = L.kd.M;
   const int ld = M + 1;
-  const TX* xg = static_cast<const TX*>(L.x);
-  for (long long e = threadIdx.x; e < nv * M; e += LM_THREADS) {
-    const long long r = e / M, m = e - r * M;
-    const float xv = ld1(xg + v0 * M + e);
+  const TX* xg = static_cast<const TX*>(L.x) + v0 * M;
+  // e < LM_BLOCK_VOX * 32: the multiply-high quotient is exact
+  for (int e = threadIdx.x; e < (int)nv * M; e += LM_THREADS) {
+    const int r = (int)__umulhi((unsigned)e, L.kd.div_m), m = e - r * M;
+    const float xv = ld1(xg + e);
     xs_all[r * ld + m] = L.x_scale ? xv * __ldg(L.x_scale + m) : xv;
   }
   __syncthreads();
@@ -692,9 +703,8 @@ __global__ void __launch_bounds__(LM_THREADS, KCS_LM_MINBLOCKS) k_lm_step(LmArgs
     act[k] = lv < nv;
     const long long v = act[k] ? v0 + lv : v0;
     vv[k] = v;
-    const int i = (int)(v % L.nx);
-    const int j = (int)((v / L.nx) % L.ny);
-    const int z = (int)(v / ((long long)L.nx * L.ny));
+    int i, j, z;
+    voxel_ijz(L, v, i, j, z);
     const float xi[4] = {L.p_in[v], L.p_in[V + v], L.p_in[2 * V + v], L.p_in[3 * V + v]};
     Normal n;
     KSum rr;
@@ -734,9 +744,8 @@ __global__ void __launch_bounds__(LM_THREADS, KCS_LM_MINBLOCKS) k_lm_step(LmArgs
   for (int k = 0; k < LM_VPT; ++k) {
     if (!act[k]) continue;
     const long long v = vv[k];
-    const int i = (int)(v % L.nx);
-    const int j = (int)((v / L.nx) % L.ny);
-    const int z = (int)(v / ((long long)L.nx * L.ny));
+    int i, j, z;
+    voxel_ijz(L, v, i, j, z);
     float gt[4], Ht;
     huber_terms(L, V, v, i, j, z, tr[k], gt, Ht);
     // Phi(trial) - Phi(current) < -TAU Phi(current)
@@ -997,6 +1006,8 @@ int kcs_map_lm_fit_nb(const kcs_kinetics_t* k, int nx, int ny, int nz, const voi
   L.beta = beta_h;
   L.delta = delta;
   L.nb3d = neighbourhood == 26 ? 1 : 0;
+  L.div_nx = div_magic64((unsigned long long)nx);
+  L.div_nxy = div_magic64((unsigned long long)nx * ny);
   const size_t smem = sizeof(float) * LM_BLOCK_VOX * (k->M + 1);
   auto kern = x_type == KCS_BF16 ? k_lm_step<__nv_bfloat16>
             : x_type == KCS_F16 ? k_lm_step<__half> : k_lm_step<float>;
