@@ -170,19 +170,25 @@ __global__ void __launch_bounds__(256) k_forward(ProjArgs p) {
   // flight at once and the accumulated values equal the plain loop's.
   float4 acc = f4(0.f);
   constexpr int U = 4;
-  for (int tb = t0; tb <= t1; tb += U) {
+  const unsigned nmin = (unsigned)n_minor;
+  // per trip: the centred major coordinate of its first step (exact: small
+  // integers and half-integers) and the image row/column of that step; within
+  // a trip the offsets are 32-bit (a plane holds fewer than 2^31 elements)
+  float tf = (float)t0 - tc;
+  const TX* xt = xz + (ptrdiff_t)t0 * s_major;
+  for (int tb = t0; tb <= t1; tb += U, tf += (float)U, xt += (ptrdiff_t)U * s_major) {
     float4 v0[U], v1[U];
     float w0[U], w1[U];
 #pragma unroll
     for (int u = 0; u < U; ++u) {
-      const int t = tb + u;
-      const float fr = minor_pos(bf, T.beta, inner_pos((float)t - tc, T.gamma, centre));
+      const bool live = tb + u <= t1;
+      const float fr = minor_pos(bf, T.beta, inner_pos(tf + (float)u, T.gamma, centre));
       const float fl = floorf(fr);
       const int j0 = (int)fl;
       const float f = fr - fl;
-      const bool in0 = t <= t1 && j0 >= 0 && j0 < n_minor;
-      const bool in1 = t <= t1 && j0 >= -1 && j0 + 1 < n_minor;
-      const TX* px = xz + (ptrdiff_t)t * s_major + (ptrdiff_t)j0 * s_minor;
+      const bool in0 = live && (unsigned)j0 < nmin;
+      const bool in1 = live && (unsigned)(j0 + 1) < nmin;
+      const TX* px = xt + (u * s_major + j0 * s_minor);
       v0[u] = in0 ? load4(px) : f4(0.f);
       v1[u] = in1 ? load4(px + s_minor) : f4(0.f);
       w0[u] = in0 ? 1.0f - f : 0.f;
