@@ -62,13 +62,15 @@ __device__ __forceinline__ void st1(__half* p, float v) { *p = __float2half_rn(f
 // tf = t - (n_major-1)/2) the ray of bin b (centred bf = b - (B-1)/2) meets the
 // fractional minor index fr = fma(bf, beta, fma(tf, gamma, (n_minor-1)/2)).
 // x-major angles step over columns (minor = rows), the others over rows.
-struct AngleTab {
+struct __align__(16) AngleTab {
   float beta;      // d fr / d bin
   float gamma;     // d fr / d major step
   float w;         // step weight h / max(|cos|, |sin|)
   int xmajor;      // 1: major axis = columns
   float inv_beta;  // 1 / beta (only to bound candidate bins; exact tests use beta)
-  float pad[3];
+  float tc;        // (n_major - 1) / 2: centre of the major axis
+  float centre;    // (n_minor - 1) / 2: centre of the minor axis
+  float rband;     // |1 / beta| + 1e-3: half-width in bins of the candidates of a voxel
 };
 
 }  // namespace kcs

@@ -574,18 +574,15 @@ __global__ void __launch_bounds__(BK_TILE * BK_TILE) k_back_bulk(ProjArgs p, int
       if (!valid || !ok) continue;
       const int a = s_a[c];
       const AngleTab T = s_T[c];
-      const int n_major = T.xmajor ? p.nx : p.ny;
-      const int n_minor = T.xmajor ? p.ny : p.nx;
       const int t = T.xmajor ? i : j;
       const int m = T.xmajor ? j : i;
-      const float tc = 0.5f * (float)(n_major - 1);
-      const float centre = 0.5f * (float)(n_minor - 1);
-      const float inner = inner_pos((float)t - tc, T.gamma, centre);
-      int b_lo, b_hi;
-      bin_range_tight(T, m, inner, bc, p.B, b_lo, b_hi);
+      const float inner = inner_pos((float)t - T.tc, T.gamma, T.centre);
+      // candidates: bins within |1/beta| (+1e-3) of the real bin u whose ray
+      // meets minor index m; the exact test below decides
+      const float u = fmaf((float)m - inner, T.inv_beta, bc);
       const int lo = s_lo[c];
-      b_lo = max(b_lo, lo);
-      b_hi = min(b_hi, lo + s_cnt[c] - 1);
+      const int b_lo = max((int)ceilf(u - T.rband), lo);
+      const int b_hi = min((int)floorf(u + T.rband), lo + s_cnt[c] - 1);
       const TY* rows = reinterpret_cast<const TY*>(sraw + (size_t)c * rows_max * RB);
       const size_t binrow = (size_t)(z * p.A + a) * p.B;
       for (int b = b_lo; b <= b_hi; ++b) {
@@ -906,7 +903,10 @@ int kcs_create_geometry(kcs_geometry_t** out, int nx, int ny, int nz, float vox_
       T.w = (float)(vox_mm / fabs(c));
       T.inv_beta = (float)(c * vox_mm / bin_mm);
     }
-    T.pad[0] = T.pad[1] = T.pad[2] = 0.f;
+    const int n_major = T.xmajor ? nx : ny, n_minor = T.xmajor ? ny : nx;
+    T.tc = 0.5f * (float)(n_major - 1);      // the kernels' own float expressions
+    T.centre = 0.5f * (float)(n_minor - 1);
+    T.rband = fabsf(T.inv_beta) + 1e-3f;
     tab[a] = T;
   }
   kcs_geometry* g = new kcs_geometry();
