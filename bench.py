@@ -76,9 +76,9 @@ LM_FLOPS_PER_VOXEL_STEP = lm_flops_per_voxel_step(frames=S.WORKLOADS["pr2"].n_fr
 # planes: every kernel touches each plane's data independently), valid while
 # the kernel's source file is unchanged (sha256 prefix); see profiles/.
 TRAFFIC = {
-    "lm_step": {"bytes": 470.58e6 * 127 / 16, "src": "kinetics.cu", "sha": "edf5aa70f0c1c05e"},
-    "bwd_osl": {"bytes": 509.16e6 * 127 / 16, "src": "projector.cu", "sha": "f126ccf36c7cd7b0"},
-    "fwd_ratio": {"bytes": 255.66e6 * 127 / 16, "src": "projector.cu", "sha": "f126ccf36c7cd7b0"},
+    "lm_step": {"bytes": 469.90e6 * 127 / 16, "src": "kinetics.cu", "sha": "206698b8831d7b22"},
+    "bwd_osl": {"bytes": 508.98e6 * 127 / 16, "src": "projector.cu", "sha": "4e430358b83c96cd"},
+    "fwd_ratio": {"bytes": 252.06e6 * 127 / 16, "src": "projector.cu", "sha": "4e430358b83c96cd"},
 }
 
 
