@@ -17,6 +17,11 @@ fit) and KCS DIRECT (the full ICM).
 
 ICM on this joint objective is not convex and the paper defines no stopping
 rule, so parity is on the trajectory for fixed iteration counts.
+
+Parity status: icm() itself is parity unpinned -- nothing outside the oracle
+fixes the trajectory of the alternation (the paper prints no values).  It
+only composes osl.osl_pass and lm.lm_fit, which are pinned in
+tests/test_oracle_osl.py and tests/test_oracle_lm.py.
 """
 from __future__ import annotations
 
