@@ -591,9 +591,12 @@ __global__ void __launch_bounds__(BK_TILE * BK_TILE) k_back_bulk(ProjArgs p, int
         const int jj = (int)fl;
         const float f = fr - fl;
         float wt = (jj == m) ? 1.0f - f : ((jj + 1 == m) ? f : 0.0f);
-        if (wt == 0.0f) continue;
+        // MODE 1 does not branch around zero weights (fewer divergent
+        // branches): its staged ratios are finite (s / ybar or 0), so a zero
+        // weight adds exactly nothing.  A caller's sinogram (MODE 0) may not be.
+        if (MODE == 0 && wt == 0.0f) continue;
         wt *= T.w;
-        if (MODE == 1 && p.bin_factor) wt *= __ldg(p.bin_factor + binrow + b);
+        if (MODE == 1 && p.bin_factor && wt != 0.0f) wt *= __ldg(p.bin_factor + binrow + b);
         const TY* row = rows + (size_t)(b - lo) * p.yq * 4;
 #pragma unroll
         for (int q = 0; q < MQ; ++q) fma4(acc[q], wt, ld4(row + q * 4));
