@@ -77,8 +77,8 @@ LM_FLOPS_PER_VOXEL_STEP = lm_flops_per_voxel_step(frames=S.WORKLOADS["pr2"].n_fr
 # the kernel's source file is unchanged (sha256 prefix); see profiles/.
 TRAFFIC = {
     "lm_step": {"bytes": 469.90e6 * 127 / 16, "src": "kinetics.cu", "sha": "206698b8831d7b22"},
-    "bwd_osl": {"bytes": 508.98e6 * 127 / 16, "src": "projector.cu", "sha": "4e430358b83c96cd"},
-    "fwd_ratio": {"bytes": 252.06e6 * 127 / 16, "src": "projector.cu", "sha": "4e430358b83c96cd"},
+    "bwd_osl": {"bytes": 509.05e6 * 127 / 16, "src": "projector.cu", "sha": "9cb7fafdca0e9c59"},
+    "fwd_ratio": {"bytes": 266.50e6 * 127 / 16, "src": "projector.cu", "sha": "9cb7fafdca0e9c59"},
 }
 
 

@@ -129,8 +129,10 @@ constexpr int LL_PARTS = 1024;   // partial sums of the log-likelihood
 
 // Forward projection of every frame of rays (z, ak, b); RATIO replaces the
 // projection by rho = s / (kappa dt n_d (P x) + r).
+constexpr int FWD_THREADS = 128;   // 4 warps per block (measured best of 64..512)
+
 template <int MQ, bool RATIO, class TX, class TC, class TY>
-__global__ void __launch_bounds__(256) k_forward(ProjArgs p) {
+__global__ void __launch_bounds__(FWD_THREADS) k_forward(ProjArgs p) {
   constexpr int RPW = 32 / MQ;
   const int lane = threadIdx.x & 31;
   const int sub = lane / MQ;
@@ -767,16 +769,17 @@ static void launch_forward_t(int MQ, const ProjArgs& p0, cudaStream_t s) {
   const int rpw = 32 / MQ;
   const long long rays = (long long)p.nz * p.n_sub * p.B;
   const long long warps = (rays + rpw - 1) / rpw;
-  const unsigned blocks = (unsigned)((warps + 7) / 8);
+  constexpr int wpb = FWD_THREADS / 32;
+  const unsigned blocks = (unsigned)((warps + wpb - 1) / wpb);
   switch (MQ) {
-    case 1: k_forward<1, RATIO, TX, TC, TY><<<blocks, 256, 0, s>>>(p); break;
-    case 2: k_forward<2, RATIO, TX, TC, TY><<<blocks, 256, 0, s>>>(p); break;
-    case 3: k_forward<3, RATIO, TX, TC, TY><<<blocks, 256, 0, s>>>(p); break;
-    case 4: k_forward<4, RATIO, TX, TC, TY><<<blocks, 256, 0, s>>>(p); break;
-    case 5: k_forward<5, RATIO, TX, TC, TY><<<blocks, 256, 0, s>>>(p); break;
-    case 6: k_forward<6, RATIO, TX, TC, TY><<<blocks, 256, 0, s>>>(p); break;
-    case 7: k_forward<7, RATIO, TX, TC, TY><<<blocks, 256, 0, s>>>(p); break;
-    case 8: k_forward<8, RATIO, TX, TC, TY><<<blocks, 256, 0, s>>>(p); break;
+    case 1: k_forward<1, RATIO, TX, TC, TY><<<blocks, FWD_THREADS, 0, s>>>(p); break;
+    case 2: k_forward<2, RATIO, TX, TC, TY><<<blocks, FWD_THREADS, 0, s>>>(p); break;
+    case 3: k_forward<3, RATIO, TX, TC, TY><<<blocks, FWD_THREADS, 0, s>>>(p); break;
+    case 4: k_forward<4, RATIO, TX, TC, TY><<<blocks, FWD_THREADS, 0, s>>>(p); break;
+    case 5: k_forward<5, RATIO, TX, TC, TY><<<blocks, FWD_THREADS, 0, s>>>(p); break;
+    case 6: k_forward<6, RATIO, TX, TC, TY><<<blocks, FWD_THREADS, 0, s>>>(p); break;
+    case 7: k_forward<7, RATIO, TX, TC, TY><<<blocks, FWD_THREADS, 0, s>>>(p); break;
+    case 8: k_forward<8, RATIO, TX, TC, TY><<<blocks, FWD_THREADS, 0, s>>>(p); break;
   }
 }
 
