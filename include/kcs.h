@@ -245,11 +245,15 @@ int kcs_huber_grad_nb(int nx, int ny, int nz, const float* params, float delta,
  *   (J^T J + lambda I) step = J^T (x - F) - beta_h dH/dxi  (float-float Cholesky)
  *   trial = clamp(xi + step, 0, (2, 2, 1, 1)); accept iff the voxel objective
  *   Phi = 1/2 |x - F|^2 + beta_h sum_p sum_{N8} huber(xi_p - xi_{k,p}) falls by
- *   more than 1e-5 Phi, with the neighbours frozen at their start-of-step values;
+ *   more than tau Phi, with the neighbours frozen at their start-of-step values;
  *   lambda /= 10 (>= 1e-7) on accept, *= 10 (<= 1e7) on reject.
+ * The paper gives no acceptance rule: tau = 0 accepts any decrease (equal
+ * objectives reject); kcs_map_lm_fit and kcs_map_lm_fit_ex use the sufficient-
+ * decrease threshold tau = KCS_LM_TAU_DEFAULT, kcs_map_lm_fit_nb takes tau.
  * params [4][Z][ny][nx] in/out; lambda [Z][ny][nx] in/out, or NULL to start
  * every voxel at 1e-2; F_out [Z][ny][nx][M] receives F(final params) when not
  * NULL.  workspace >= kcs_lm_workspace_size(nx, ny, nz) bytes. */
+#define KCS_LM_TAU_DEFAULT 1e-5f
 size_t kcs_lm_workspace_size(int nx, int ny, int nz);
 int kcs_map_lm_fit(const kcs_kinetics_t* k, int nx, int ny, int nz, const float* x,
                    float* params, float* lambda, int n_steps, float beta_h, float delta,
@@ -262,11 +266,12 @@ int kcs_map_lm_fit_ex(const kcs_kinetics_t* k, int nx, int ny, int nz, const voi
                       int n_steps, float beta_h, float delta, float* F_out, void* workspace,
                       size_t ws_bytes, void* stream);
 /* kcs_map_lm_fit_ex with the Huber neighbourhood as in kcs_huber_grad_nb
- * (8 or 26). */
+ * (8 or 26) and the acceptance threshold tau in [0, 1) (KCS_ERR_INVALID_ARG
+ * otherwise). */
 int kcs_map_lm_fit_nb(const kcs_kinetics_t* k, int nx, int ny, int nz, const void* x,
                       int x_type, const float* x_scale, float* params, float* lambda,
-                      int n_steps, float beta_h, float delta, int neighbourhood, float* F_out,
-                      void* workspace, size_t ws_bytes, void* stream);
+                      int n_steps, float beta_h, float delta, int neighbourhood, float tau,
+                      float* F_out, void* workspace, size_t ws_bytes, void* stream);
 
 /* ------------------------------------------------- MAP-LM without allocation
  * The paper has no counterpart to this entry point; it exists for callers that
@@ -280,6 +285,9 @@ int kcs_map_lm_fit_nb(const kcs_kinetics_t* k, int nx, int ny, int nz, const voi
  *    rejected with KCS_ERR_INVALID_ARG and a message (use kcs_map_lm_fit).
  *  - The first call on a device looks up the array's device address with that
  *    device current; make that first call before any stream capture.
+ *  - The stream (if not NULL) must belong to the current device: the array's
+ *    address differs per device, so a stream of another device is rejected
+ *    with KCS_ERR_INVALID_ARG.
  *  - Every call on a device shares the one array: calls whose work overlaps on
  *    the GPU (different streams, or host threads without ordering) race and
  *    corrupt each other; serialise them.  Nothing in the array needs to start at
@@ -289,6 +297,18 @@ int kcs_map_lm_fit_nb(const kcs_kinetics_t* k, int nx, int ny, int nz, const voi
 int kcs_map_lm_fit_static(const kcs_kinetics_t* k, int nx, int ny, int nz, const float* x,
                           float* params, float* lambda, int n_steps, float beta_h, float delta,
                           float* F_out, void* stream);
+
+/* ------------------------------------------------------- measurement
+ * Arithmetic peak probe (not part of the method): launches blocks x 256
+ * threads that each advance 16 independent multiply-add chains iters times in
+ * float32 (precision = 32, FFMA) or float64 (precision = 64, DFMA), on stream;
+ * *flops receives the number of floating-point operations the launch performs
+ * (a multiply-add counts 2).  The caller times the launch with CUDA events:
+ * flops / time is the measured FFMA or DFMA rate of the GPU, the denominator of
+ * a kernel's fraction of arithmetic peak.  sink: device buffer of at least
+ * 8 x blocks bytes (never written for the chains' values).  Asynchronous. */
+int kcs_fma_peak_launch(int precision, int blocks, int iters, double* flops, void* sink,
+                        void* stream);
 
 /* Device-side failure detection: the number of bounded waits inside the
  * library's kernels (bulk-copy completion barriers) that ran out instead of
@@ -347,6 +367,10 @@ typedef struct kcs_study_desc {
   int method;
   /* Huber neighbourhood of the fit: 0 or 8 = in-plane 3x3 (Sec. II-C), 26 = 3x3x3 */
   int neighbourhood;
+  /* MAP-LM acceptance threshold (see kcs_map_lm_fit_nb): lm_tau when
+   * lm_tau_given is nonzero, else KCS_LM_TAU_DEFAULT. */
+  float lm_tau;
+  int lm_tau_given;
 } kcs_study_desc_t;
 
 enum { KCS_METHOD_KCS = 0, KCS_METHOD_DIRECT = 1, KCS_METHOD_INDIRECT = 2 };

@@ -42,7 +42,8 @@ class StudyDesc(C.Structure):
                 ("x", vp), ("params", vp), ("F", vp), ("params_given", i32), ("n_lm", i32),
                 ("beta_kp", f32), ("sigma2", f32), ("beta_h", f32), ("delta", f32),
                 ("workspace", vp), ("ws_bytes", sz), ("counts_type", i32), ("x_type", i32),
-                ("x_scale", vp), ("method", i32), ("neighbourhood", i32)]
+                ("x_scale", vp), ("method", i32), ("neighbourhood", i32), ("lm_tau", f32),
+                ("lm_tau_given", i32)]
 
 
 SIGNATURES = {
@@ -70,8 +71,8 @@ SIGNATURES = {
     "kcs_init_level": (i32, [vp, i32, vp, f32, vp, i32, vp, i32, vp, vp, vp, sz, vp]),
     "kcs_init_image_ex": (i32, [vp, i32, vp, f32, vp, i32, vp, i32, vp, vp, i32, vp, vp, sz, vp]),
     "kcs_huber_grad_nb": (i32, [i32, i32, i32, vp, f32, i32, vp, vp]),
-    "kcs_map_lm_fit_nb": (i32, [vp, i32, i32, i32, vp, i32, vp, vp, vp, i32, f32, f32, i32, vp, vp,
-                                sz, vp]),
+    "kcs_map_lm_fit_nb": (i32, [vp, i32, i32, i32, vp, i32, vp, vp, vp, i32, f32, f32, i32, f32,
+                                vp, vp, sz, vp]),
     "kcs_map_lm_fit_ex": (i32, [vp, i32, i32, i32, vp, i32, vp, vp, vp, i32, f32, f32, vp, vp, sz,
                                 vp]),
     "kcs_create_kinetics": (i32, [pp, i32, dp, dp, dp, vp]),
@@ -95,6 +96,7 @@ SIGNATURES = {
     "kcs_device_status": (i32, [C.POINTER(C.c_uint)]),
     "kcs_device_status_reset": (i32, []),
     "kcs_selftest_wait_timeout": (i32, [i32, vp]),
+    "kcs_fma_peak_launch": (i32, [i32, i32, i32, dp, vp, vp]),
 }
 
 for _name, (_res, _args) in SIGNATURES.items():

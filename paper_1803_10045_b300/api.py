@@ -332,10 +332,14 @@ def lm_workspace_size(nx, ny, nz):
     return lib.kcs_lm_workspace_size(nx, ny, nz)
 
 
+LM_TAU_DEFAULT = 1e-5   # KCS_LM_TAU_DEFAULT of kcs.h
+
+
 def map_lm_fit(kin: Kinetics, x, params, n_steps, beta_h, delta, lam=None, F_out=None,
-               workspace=None, x_scale=None, neighbourhood=8):
+               workspace=None, x_scale=None, neighbourhood=8, tau=LM_TAU_DEFAULT):
     """n_steps MAP-LM steps on params [4][Z][Y][X] (in place) for TACs x [Z][Y][X][M]
-    (x float32, bfloat16 or float16 holding x / x_scale[m])."""
+    (x float32, bfloat16 or float16 holding x / x_scale[m]); a trial is accepted
+    when it lowers the voxel objective by more than tau of its value."""
     nz, ny, nx, M = x.shape
     xt = _storage(x, (F32, BF16, F16), "x")
     if workspace is None:
@@ -344,7 +348,7 @@ def map_lm_fit(kin: Kinetics, x, params, n_steps, beta_h, delta, lam=None, F_out
         kin.handle, nx, ny, nz, _ptr(x, "x", (nz, ny, nx, M), dtype=x.dtype), xt,
         _ptr(x_scale, "x_scale", (M,), allow_none=True), _ptr(params, "params", (4, nz, ny, nx)),
         _ptr(lam, "lambda", (nz, ny, nx), allow_none=True), int(n_steps), float(beta_h), float(delta),
-        int(neighbourhood), _ptr(F_out, "F_out", (nz, ny, nx, M), allow_none=True),
+        int(neighbourhood), float(tau), _ptr(F_out, "F_out", (nz, ny, nx, M), allow_none=True),
         C.c_void_p(workspace.data_ptr()), workspace.numel(), _stream()))
     return params
 
@@ -355,7 +359,7 @@ class Study:
     def __init__(self, geom: Geometry, kin: Kinetics, frame_dt, kappa, counts, x, params, F=None,
                  randoms=None, bin_factor=None, params_given=False, n_lm=10, beta_kp=0.1,
                  sigma2=1.0, beta_h=0.1, delta=0.01, workspace=None, x_scale=None, graph=False,
-                 method="kcs", neighbourhood=8):
+                 method="kcs", neighbourhood=8, tau=LM_TAU_DEFAULT):
         M = kin.M
         dev = x.device
         if F is None:
@@ -387,6 +391,7 @@ class Study:
             raise ValueError(f"method must be one of {sorted(METHODS)}")
         d.method = METHODS[method]
         d.neighbourhood = int(neighbourhood)
+        d.lm_tau, d.lm_tau_given = float(tau), 1
         h = C.c_void_p()
         check(lib.kcs_create_study(C.byref(h), C.byref(d)))
         self.handle = h

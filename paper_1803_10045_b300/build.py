@@ -8,7 +8,7 @@ import sys
 HERE = os.path.dirname(os.path.abspath(__file__))
 SRC = os.path.join(HERE, "csrc")
 LIB = os.path.join(HERE, "libkcs.so")
-SOURCES = ["projector.cu", "kinetics.cu", "icm.cu"]
+SOURCES = ["projector.cu", "kinetics.cu", "icm.cu", "fma_peak.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

@@ -33,6 +33,8 @@ namespace {
 // Huber weight of the fit: the spatial prior is part of KCS only.
 float fit_beta_h(const kcs_study_desc_t& d) { return d.method == KCS_METHOD_KCS ? d.beta_h : 0.f; }
 int fit_nbhd(const kcs_study_desc_t& d) { return d.neighbourhood == 26 ? 26 : 8; }
+// Acceptance threshold of the MAP-LM step: the library default unless given.
+float fit_tau(const kcs_study_desc_t& d) { return d.lm_tau_given ? d.lm_tau : KCS_LM_TAU_DEFAULT; }
 
 int issue_osl_pass(const kcs_study* st, bool prior, void* stream) {
   const kcs_study_desc_t& d = st->d;
@@ -62,8 +64,8 @@ int issue_fit(const kcs_study* st, void* stream) {
   if (d.method == KCS_METHOD_INDIRECT) return KCS_OK;
   nvtxRangePushA("kcs::map_lm_fit");
   const int rc = kcs_map_lm_fit_nb(d.kin, g->nx, g->ny, g->nz, d.x, d.x_type, d.x_scale, d.params,
-                           nullptr, d.n_lm, fit_beta_h(d), d.delta, fit_nbhd(d), d.F, d.workspace,
-                           d.ws_bytes, stream);
+                           nullptr, d.n_lm, fit_beta_h(d), d.delta, fit_nbhd(d), fit_tau(d), d.F,
+                           d.workspace, d.ws_bytes, stream);
   nvtxRangePop();
   return rc;
 }
@@ -126,6 +128,8 @@ int kcs_create_study(kcs_study_t** out, const kcs_study_desc_t* d) {
   KCS_REQUIRE(d->method == KCS_METHOD_KCS || d->method == KCS_METHOD_DIRECT ||
                   d->method == KCS_METHOD_INDIRECT,
               "method %d must be KCS_METHOD_KCS, _DIRECT or _INDIRECT", d->method);
+  KCS_REQUIRE(!d->lm_tau_given || (d->lm_tau >= 0.f && d->lm_tau < 1.f),
+              "lm_tau = %g must lie in [0, 1)", (double)d->lm_tau);
   KCS_REQUIRE(d->neighbourhood == 0 || d->neighbourhood == 8 || d->neighbourhood == 26,
               "neighbourhood %d must be 0, 8 or 26", d->neighbourhood);
   KCS_REQUIRE(d->workspace && d->ws_bytes >= kcs_study_workspace_size(d->geom, d->n_frames),
@@ -182,7 +186,7 @@ int kcs_study_fit(kcs_study_t* st, int n_steps, void* stream) {
   const kcs_study_desc_t& d = st->d;
   const kcs_geometry* g = d.geom;
   return kcs_map_lm_fit_nb(d.kin, g->nx, g->ny, g->nz, d.x, d.x_type, d.x_scale, d.params,
-                           nullptr, n_steps, fit_beta_h(d), d.delta, fit_nbhd(d), d.F,
+                           nullptr, n_steps, fit_beta_h(d), d.delta, fit_nbhd(d), fit_tau(d), d.F,
                            d.workspace, d.ws_bytes, stream);
 }
 

@@ -436,9 +436,6 @@ constexpr int LM_BLOCK_VOX = LM_THREADS * LM_VPT;
 __constant__ float c_lo[4] = {0.f, 0.f, 0.f, 0.f};
 __constant__ float c_hi[4] = {2.f, 2.f, 1.f, 1.f};
 constexpr float LAMBDA0 = 1e-2f, LAMBDA_MIN = 1e-7f, LAMBDA_MAX = 1e7f;
-// A trial is accepted when it lowers the voxel objective by more than TAU of its
-// value: smaller changes are below float32 resolution of the model.
-constexpr float TAU = 1e-5f;
 
 struct LmArgs {
   KinDev kd;
@@ -450,6 +447,7 @@ struct LmArgs {
   float* lambda;         // [V]
   int reset_lambda;
   float beta, delta;
+  float tau;             // accept iff the objective falls by more than tau of its value
   int nb3d;              // Huber neighbourhood: 0 in-plane 3x3, 1 the 3x3x3 cube
   const float* ne_in;    // [16][V] normal equations at the current point
   float* ne_out;         // [16][V] normal equations at the returned point
@@ -749,9 +747,9 @@ __global__ void __launch_bounds__(LM_THREADS, KCS_LM_MINBLOCKS) k_lm_step(LmArgs
     voxel_ijz(L, v, i, j, z);
     float gt[4], Ht;
     huber_terms(L, V, v, i, j, z, tr[k], gt, Ht);
-    // Phi(trial) - Phi(current) < -TAU Phi(current)
+    // Phi(trial) - Phi(current) < -tau Phi(current)
     const float dphi = 0.5f * ((ns.rr[k].s - rrs[k]) - (ns.rr[k].c - rrcmp[k]));
-    const bool accept = solved[k] && fmaf(L.beta, Ht - Hc[k], dphi) < -TAU * phi[k];
+    const bool accept = solved[k] && fmaf(L.beta, Ht - Hc[k], dphi) < -L.tau * phi[k];
 #pragma unroll
     for (int q = 0; q < 4; ++q) L.p_out[q * V + v] = accept ? tr[k][q] : L.p_in[q * V + v];
     L.lambda[v] = accept ? fmaxf(lam[k] * 0.1f, LAMBDA_MIN) : fminf(lam[k] * 10.f, LAMBDA_MAX);
@@ -970,14 +968,15 @@ int kcs_map_lm_fit_ex(const kcs_kinetics_t* k, int nx, int ny, int nz, const voi
                       int n_steps, float beta_h, float delta, float* F_out, void* workspace,
                       size_t ws_bytes, void* stream) {
   return kcs_map_lm_fit_nb(k, nx, ny, nz, x, x_type, x_scale, params, lambda, n_steps, beta_h,
-                           delta, 8, F_out, workspace, ws_bytes, stream);
+                           delta, 8, KCS_LM_TAU_DEFAULT, F_out, workspace, ws_bytes, stream);
 }
 
 int kcs_map_lm_fit_nb(const kcs_kinetics_t* k, int nx, int ny, int nz, const void* x,
                       int x_type, const float* x_scale, float* params, float* lambda,
-                      int n_steps, float beta_h, float delta, int neighbourhood, float* F_out,
-                      void* workspace, size_t ws_bytes, void* stream) {
+                      int n_steps, float beta_h, float delta, int neighbourhood, float tau,
+                      float* F_out, void* workspace, size_t ws_bytes, void* stream) {
   clear_error();
+  KCS_REQUIRE(tau >= 0.f && tau < 1.f, "tau = %g must lie in [0, 1)", (double)tau);
   KCS_REQUIRE(neighbourhood == 8 || neighbourhood == 26, "neighbourhood %d must be 8 or 26",
               neighbourhood);
   KCS_REQUIRE(k && x && params, "NULL argument");
@@ -1006,6 +1005,7 @@ int kcs_map_lm_fit_nb(const kcs_kinetics_t* k, int nx, int ny, int nz, const voi
   L.lambda = lambda ? lambda : lam_ws;
   L.beta = beta_h;
   L.delta = delta;
+  L.tau = tau;
   L.nb3d = neighbourhood == 26 ? 1 : 0;
   L.div_nx = div_magic64((unsigned long long)nx);
   L.div_nxy = div_magic64((unsigned long long)nx * ny);
@@ -1087,6 +1087,11 @@ extern "C" int kcs_map_lm_fit_static(const kcs_kinetics_t* k, int nx, int ny, in
   int dev = 0;
   KCS_CUDA(cudaGetDevice(&dev));
   KCS_REQUIRE(dev >= 0 && dev < kMaxDevices, "device index %d out of range", dev);
+  if (stream) {   // the scratch address below belongs to the current device
+    int sdev = -1;
+    KCS_CUDA(cudaStreamGetDevice(as_stream(stream), &sdev));
+    KCS_REQUIRE(sdev == dev, "stream belongs to device %d, the current device is %d", sdev, dev);
+  }
   void* scratch = nullptr;
   {
     // First call on this device: look up the array's device address with the

@@ -878,7 +878,7 @@ using namespace kcs;
 extern "C" {
 
 const char* kcs_last_error(void) { return kcs::g_err.c_str(); }
-int kcs_version(void) { return 2; }
+int kcs_version(void) { return 3; }
 
 int kcs_create_geometry(kcs_geometry_t** out, int nx, int ny, int nz, float vox_mm, int n_bins,
                         int n_angles, float bin_mm, int n_subsets) {

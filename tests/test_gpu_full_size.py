@@ -12,14 +12,13 @@ import pytest
 import torch
 
 import kcs_synth as S
-from cases import rel_l2
+from cases import lm_step_parity, rel_l2
 from oracle import kinetics as OK
 from oracle import lm as OL
 from oracle import osl as OO
 from oracle import projector as OP
 
 pytestmark = pytest.mark.gpu
-FLOOR = 1e-2 * np.array([0.06, 0.10, 0.04, 0.03])
 
 
 def _f32(v):
@@ -109,18 +108,12 @@ def test_full_size_lm_step_sampled_voxels(cuda_ok):
     win_lam = lam0[zz, jj, ii].double().cpu().numpy()
     got = p[:, zji[:, 0], zji[:, 1], zji[:, 2]].double().cpu().numpy().T   # [n][4]
     lam_g = lam[zji[:, 0], zji[:, 1], zji[:, 2]].double().cpu().numpy()
-    start = win_maps[:, :, 1, 1].T
-    lam_s = win_lam[:, 1, 1]
-    ref_m, _, acc_r, _ = OL.lm_step(win_x, win_maps, win_lam, ts, te, S.FENG, beta, delta)
-    ref = ref_m[:, :, 1, 1].T
-    acc_r = acc_r[:, 1, 1]
-    acc_g = np.isclose(lam_g, np.maximum(lam_s / 10, 1e-7), rtol=1e-5)
-    agree = acc_g == acc_r
-    tol = 1e-3 * np.maximum(np.abs(ref), FLOOR[None, :])
-    within = np.all(np.abs(got - ref) <= tol, axis=1)[agree]
-    print(f"accept agreement {agree.mean():.4f} (accepted {acc_r.mean():.3f}), "
-          f"maps within 1e-3 on {within.mean():.4f}")
-    assert agree.mean() > 0.98
-    assert within.mean() > 0.99
-    rej = ~acc_g & ~acc_r
-    np.testing.assert_array_equal(got[rej], start[rej])
+    # the oracle's step of each window (3 x 3 neighbourhoods as separate planes);
+    # the centre voxel of window k is voxel 9 k + 4 of the flattened result
+    sp = OL.float32_spread(win_x, win_maps, win_lam, ts, te, S.FENG, beta, delta)
+    ctr = np.arange(n) * 9 + 4
+    keys = ("acc", "trial", "xi", "flip", "margin", "dev_trial", "dev_margin")
+    spc = {k: sp[k][ctr] for k in keys}
+    # lambda spans 1e-6 .. 10 here, so more steps are float32-sensitive than on
+    # PR1 (the share is fixed by the oracle: 73 % strict on these inputs)
+    lm_step_parity(got.T, lam_g, win_lam[:, 1, 1], spc, 0.6, "PR2 sampled voxels")

@@ -2,12 +2,13 @@
 
 Tolerance derivation: the kernel evaluates per-cell cubic Hermite
 interpolants of a float64 table of the frame averages (a = k2 + k3, spacing
-1/512: interpolation error ~1e-8 of a frame's range for the values, ~5e-6 of
-the largest slope for the a-derivatives, which come from the same cubics) and
-rounds the coefficients and a handful of fused multiply-adds to float32 (a few
-1e-7), so F is held to 1e-5 relative to the frame's values; J entries are
-compared with an absolute error (1e-4) relative to the voxel's largest
-Jacobian entry.
+1/512), with the coefficients and a handful of fused multiply-adds in float32.
+A CPU emulation of that table against the exact model puts the values within
+2.3e-7 of each voxel's largest |F| and the derivative columns within 3.1e-6 of
+each column's largest entry (the slopes carry the cubic's truncation).  The
+tests hold F to 1e-6 of the voxel's largest |F| and every Jacobian entry to
+2e-5 of the voxel's largest Jacobian entry (dF/dk3 = -(1-Vb) K1 k2 B' is
+exactly 0 at k2 = 0, so it is measured against the row, not its own column).
 """
 import numpy as np
 import pytest
@@ -55,13 +56,13 @@ def _check(ts, te, xi):
     J = J.double().cpu().numpy()
     # the oracle sees the parameters the GPU saw (float32-rounded)
     Fr, Jr = OK.model(xi.astype(np.float32).astype(np.float64), ts, te, S.FENG)
-    scale = np.maximum(np.abs(Fr), 1e-3 * np.abs(Fr).max())
-    assert np.max(np.abs(F - Fr) / scale) < 1e-5
-    # per voxel, relative to its largest Jacobian entry: dF/dk3 is a difference of
-    # two terms of that size and is exactly 0 at a = 0
-    row = np.abs(Jr).max(axis=(1, 2))[:, None] + 1e-30
-    for q in range(4):
-        assert np.max(np.abs(J[:, :, q] - Jr[:, :, q]) / row) < 1e-4, q
+    eF = np.abs(F - Fr).max(axis=1) / np.abs(Fr).max(axis=1).clip(1e-30)
+    row = np.abs(Jr).max(axis=(1, 2)) + 1e-30
+    eJ = np.abs(J - Jr).max(axis=1) / row[:, None]
+    print(f"max |dF| / max|F| {eF.max():.2e}; max |dJ_q| / max|J| "
+          + " ".join(f"{eJ[:, q].max():.2e}" for q in range(4)))
+    assert eF.max() < 1e-6
+    assert eJ.max() < 2e-5
 
 
 @pytest.mark.parametrize("sched", list(SCHEDS))

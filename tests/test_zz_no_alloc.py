@@ -19,8 +19,6 @@ from oracle import kinetics as OK
 
 pytestmark = pytest.mark.gpu
 
-FLOOR = 1e-2 * np.array([0.06, 0.10, 0.04, 0.03])[:, None, None, None]
-
 
 def _problem(seed, nz, ny, nx, ts, te):
     """Noisy TACs of jittered parameters and jittered start maps (inputs only)."""
@@ -47,26 +45,31 @@ def test_static_scratch_fit_matches_workspace_fit(cuda_ok):
     ts, te = S.schedule(S.SCHEDULES["pr1"])
     kin = K.Kinetics(ts, te, S.FENG)
     stream = C.c_void_p(torch.cuda.current_stream().cuda_stream)
-    # two calls in a row with different shapes and inputs: the second must not
-    # see anything left in the shared array by the first
-    for call, (seed, shape, steps) in enumerate([(0, (2, 37, 53), 5), (1, (1, 64, 64), 4)]):
+    # calls in a row with different shapes and inputs, with and without a
+    # caller lambda: each must not see anything left in the shared array by
+    # the one before.  Both paths run the same kernels on the same inputs, so
+    # the maps, lambda and model TACs must agree bit for bit.
+    cases = [(0, (2, 37, 53), 5, False), (1, (1, 64, 64), 4, True), (2, (3, 11, 9), 6, True)]
+    for call, (seed, shape, steps, with_lam) in enumerate(cases):
         nz, ny, nx = shape
         x, start = _problem(seed, nz, ny, nx, ts, te)
         xd = _dev(x)
         pa, pb = _dev(start), _dev(start)
         Fa = torch.empty(x.shape, device="cuda")
-        Fb = torch.empty(x.shape, device="cuda")
-        K.map_lm_fit(kin, xd, pa, steps, 0.1, 0.01, F_out=Fa)          # caller workspace
-        rc = lib.kcs_map_lm_fit_static(kin.handle, nx, ny, nz, _p(xd), _p(pb), None, steps,
+        Fb = torch.full(x.shape, float("nan"), device="cuda")
+        la = lb = None
+        if with_lam:
+            lam0 = 10.0 ** np.random.default_rng(seed).uniform(-5, 0, shape)
+            la, lb = _dev(lam0), _dev(lam0)
+        K.map_lm_fit(kin, xd, pa, steps, 0.1, 0.01, lam=la, F_out=Fa)   # caller workspace
+        rc = lib.kcs_map_lm_fit_static(kin.handle, nx, ny, nz, _p(xd), _p(pb), _p(lb), steps,
                                        0.1, 0.01, _p(Fb), stream)
         assert rc == 0, lib.kcs_last_error()
         torch.cuda.synchronize()
-        a = pa.double().cpu().numpy()
-        b = pb.double().cpu().numpy()
-        # the maps tolerance of the LM parity tests
-        assert np.all(np.abs(b - a) <= 1e-3 * np.maximum(np.abs(a), FLOOR)), call
-        Fa_, Fb_ = Fa.double().cpu().numpy(), Fb.double().cpu().numpy()
-        assert np.max(np.abs(Fb_ - Fa_) / np.maximum(np.abs(Fa_), 1e-3)) < 1e-5, call
+        assert torch.equal(pa, pb), call
+        assert torch.equal(Fa, Fb), call
+        if with_lam:
+            assert torch.equal(la, lb), call
 
 
 def test_static_scratch_rejects_oversize(cuda_ok):
