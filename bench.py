@@ -344,6 +344,10 @@ def run_ours(args):
     for _ in range(args.warmup):
         st.iterate(1)
     torch.cuda.synchronize()
+    # measured FFMA rate of this GPU (the LM kernel's arithmetic roofline),
+    # outside the timed region
+    from paper_1803_10045_b300.peaks import measure_fma_peak
+    fp32_meas = measure_fma_peak(32, target_ms=60.0)
 
     # ---- timed region: the kernels icm_iterate issues, with events between them
     S_ = W.n_subsets
@@ -437,13 +441,21 @@ def run_ours(args):
                          "frac_hbm": round(alg[name] / (avg * 1e-3) / 1e9 / hbm, 4),
                          "traffic_GB": _traffic(name) if args.storage == "f32" else None}
     dom = max(kernels, key=lambda n: kernels[n]["share"])
-    fp32_peak = N_SM * FP32_LANES_PER_SM * 2 * smax * 1e6 / 1e12
+    fp32_peak = fp32_meas["flops_per_s"] / 1e12
+    fp32_src = (f"measured FFMA rate, kcs_fma_peak_launch ({fp32_meas['blocks']} blocks x 256 "
+                f"threads x 16 chains, {fp32_meas['ms']} ms); unit-count figure {N_SM} SM x "
+                f"{FP32_LANES_PER_SM} lanes x 2 x {smax:.0f} MHz = "
+                f"{N_SM * FP32_LANES_PER_SM * 2 * smax * 1e6 / 1e12:.1f}")
+    lm_tf = V * LM_FLOPS_PER_VOXEL_STEP / (kernels["lm_step"]["avg_ms"] * 1e-3) / 1e12
+    kernels["lm_step"].update({"flop_per_voxel_step": LM_FLOPS_PER_VOXEL_STEP,
+                               "tflops": round(lm_tf, 2), "fp32_peak_tflops": round(fp32_peak, 2),
+                               "frac_fp32": round(lm_tf / fp32_peak, 4)})
     if dom == "lm_step":
-        ach = V * LM_FLOPS_PER_VOXEL_STEP / (kernels[dom]["avg_ms"] * 1e-3) / 1e12
+        ach = lm_tf
         roof = {"bound": "alu", "kernel": dom, "achieved": round(ach, 2),
                 "peak": round(fp32_peak, 1), "unit": "TFLOP/s", "frac": round(ach / fp32_peak, 4),
                 "traffic": kernels[dom]["traffic_GB"], "traffic_unit": "GB/launch",
-                "peak_source": f"FP32 FMA {N_SM} SM x {FP32_LANES_PER_SM} lanes x 2 x {smax:.0f} MHz"}
+                "peak_source": fp32_src}
     else:
         ach = kernels[dom]["alg_GBps"]
         roof = {"bound": "hbm", "kernel": dom, "achieved": ach, "peak": hbm, "unit": "GB/s",
@@ -476,6 +488,15 @@ def run_ours(args):
                 "d2h_bytes_per_step": params.numel() * 4},
         "finite": ok,
     }
+    if world == 1 and not args.no_serve:
+        # bounded PR5 serving leg: p50/p99 study latency under a Poisson stream
+        summ, det = serve_stream(K, torch, args.serve_requests, args.mean_gap, "f32",
+                                 args.budget_gb, args.max_active, args.serve_iters, args.policy)
+        out["serving"] = dict({
+            "studies_s": round(summ["studies_per_s"], 4), "p50_s": round(summ["p50_s"], 3),
+            "p99_s": round(summ["p99_s"], 3), "completed": summ["completed"],
+            "rejected": summ["rejected"], "makespan_s": round(summ["makespan_s"], 2),
+            "workload": SERVE_WORKLOAD}, **det)
     if not args.no_cpu_baseline:
         out["cpu_baseline"] = oracle_sample()
         out["cpu_baseline"]["cpu"] = _cpu_model()
@@ -521,6 +542,48 @@ def _serve_template(K, torch, name, storage, seed):
     return g, kin, dt, kappa, host, r.contiguous()
 
 
+def serve_stream(K, torch, requests, mean_gap, storage, budget_gb, max_active, serve_iters,
+                 policy, seed=0):
+    """Serve `requests` studies of the three PR5 size classes arriving as a
+    Poisson stream (mean gap mean_gap s) inside an HBM budget; returns the
+    summary (studies/s, arrival->done latency percentiles) and details."""
+    from paper_1803_10045_b300.serving import KcsExecutor, Server, StudyRequest, summarize
+    tmpl = {n: _serve_template(K, torch, n, storage, i) for i, n in enumerate(SERVE_CLASSES)}
+    rng = np.random.default_rng(seed)
+    arrivals = np.cumsum(rng.exponential(mean_gap, requests))
+    arrivals -= arrivals[0]
+    names = list(SERVE_CLASSES)
+    kinds = rng.integers(0, len(names), requests)
+    reqs = []
+    for rid, (t, c) in enumerate(zip(arrivals, kinds)):
+        g, kin, dt, kappa, host, r = tmpl[names[c]]
+        reqs.append(StudyRequest(rid, float(t), g, kin, dt, kappa, host, randoms=r,
+                                 n_iter=serve_iters, n_lm=N_LM, beta_kp=beta_kp_for(kappa),
+                                 beta_h=BETA_H, delta=DELTA, storage=storage))
+    budget = int(budget_gb * 1e9)
+    ex = KcsExecutor(budget, max_active)
+    torch.cuda.synchronize()
+    srv = Server(ex, budget, max_active, policy=policy)
+    recs = srv.run(reqs)
+    torch.cuda.synchronize()
+    summ = summarize(recs)
+    per = {}
+    for rec, c in zip(recs, kinds):
+        if rec.status == "done":
+            per.setdefault(names[c], []).append(rec.latency)
+    return summ, {
+        "requests": requests, "mean_gap_s": mean_gap, "storage": storage,
+        "budget_gb": budget_gb, "max_active": max_active, "icm_iterations": serve_iters,
+        "policy": policy, "peak_arena_gb": round(srv.arena.peak / 1e9, 2),
+        "class_counts": {n: int((kinds == i).sum()) for i, n in enumerate(names)},
+        "latency_by_class_p50_s": {n: round(float(np.percentile(v, 50)), 3)
+                                   for n, v in per.items()}}
+
+
+SERVE_WORKLOAD = ("PR5: Poisson arrivals, sizes 128^2x32x12 / 256^2x64x16 / 344^2x127x24 "
+                  "uniformly, ICM x 10 LM steps each")
+
+
 def run_serve(args):
     """Config PR5: a stream of studies of three sizes with Poisson arrivals
     served inside an HBM budget (continuous batching at ICM-iteration
@@ -528,51 +591,21 @@ def run_serve(args):
     import torch
 
     import paper_1803_10045_b300 as K
-    from paper_1803_10045_b300.serving import KcsExecutor, Server, StudyRequest, summarize
     torch.cuda.set_device(0)
-    tmpl = {n: _serve_template(K, torch, n, args.storage, i)
-            for i, n in enumerate(SERVE_CLASSES)}
-    rng = np.random.default_rng(0)
-    arrivals = np.cumsum(rng.exponential(args.mean_gap, args.requests))
-    arrivals -= arrivals[0]
-    names = list(SERVE_CLASSES)
-    kinds = rng.integers(0, len(names), args.requests)
-    reqs = []
-    for rid, (t, c) in enumerate(zip(arrivals, kinds)):
-        g, kin, dt, kappa, host, r = tmpl[names[c]]
-        reqs.append(StudyRequest(rid, float(t), g, kin, dt, kappa, host, randoms=r,
-                                 n_iter=args.serve_iters, n_lm=N_LM, beta_kp=beta_kp_for(kappa),
-                                 beta_h=BETA_H, delta=DELTA, storage=args.storage))
-    budget = int(args.budget_gb * 1e9)
-    ex = KcsExecutor(budget, args.max_active)
-    torch.cuda.synchronize()
     sampler = ClockSampler(0)
     sampler.start()
-    srv = Server(ex, budget, args.max_active, policy=args.policy)
-    recs = srv.run(reqs)
-    torch.cuda.synchronize()
+    summ, det = serve_stream(K, torch, args.requests, args.mean_gap, args.storage,
+                             args.budget_gb, args.max_active, args.serve_iters, args.policy)
     clocks = sampler.stop()
-    summ = summarize(recs)
-    per = {}
-    for rec, c in zip(recs, kinds):
-        if rec.status == "done":
-            per.setdefault(names[c], []).append(rec.latency)
+    by_class = det.pop("latency_by_class_p50_s")
     print(json.dumps({
         "metric": "studies/s (PR5 serving)", "value": round(summ["studies_per_s"], 4),
         "unit": "studies/s", "n_gpus": 1, "higher_is_better": True,
         "p50_s": round(summ["p50_s"], 3), "p99_s": round(summ["p99_s"], 3),
         "completed": summ["completed"], "rejected": summ["rejected"],
         "makespan_s": round(summ["makespan_s"], 2), "dtype": "f32", "data": "synthetic",
-        "config": {"workload": "PR5: Poisson arrivals, sizes 128^2x32x12 / 256^2x64x16 / "
-                               "344^2x127x24 uniformly, ICM x 10 LM steps each",
-                   "requests": args.requests, "mean_gap_s": args.mean_gap,
-                   "storage": args.storage, "budget_gb": args.budget_gb,
-                   "max_active": args.max_active, "icm_iterations": args.serve_iters,
-                   "policy": args.policy,
-                   "peak_arena_gb": round(srv.arena.peak / 1e9, 2),
-                   "class_counts": {n: int((kinds == i).sum()) for i, n in enumerate(names)}},
-        "latency_by_class_p50_s": {n: round(float(np.percentile(v, 50)), 3)
-                                   for n, v in per.items()},
+        "config": dict({"workload": SERVE_WORKLOAD}, **det),
+        "latency_by_class_p50_s": by_class,
         "clocks": clocks}))
 
 
@@ -728,6 +761,10 @@ def main():
     ap.add_argument("--serve", action="store_true",
                     help="config PR5: serve a Poisson stream of studies of three sizes")
     ap.add_argument("--requests", type=int, default=200)
+    ap.add_argument("--serve-requests", type=int, default=40,
+                    help="requests of the serving leg of the default line")
+    ap.add_argument("--no-serve", action="store_true",
+                    help="leave the serving leg out of the default line")
     ap.add_argument("--mean-gap", type=float, default=0.5)
     ap.add_argument("--budget-gb", type=float, default=32.0)
     ap.add_argument("--max-active", type=int, default=16)

@@ -2,16 +2,16 @@
 
 Two checks.  (1) Teacher-forced: from the same image and model TACs, one
 OSL pass with the kinetics-derived prior switched on matches the oracle within
-the image tolerance (1e-4 relative L2).  (2) End to end over 5 iterations the
-float32 and float64 runs are different trajectories of the same non-convex
-algorithm (LM accept decisions inside float32 resolution differ and the maps
-of poorly determined voxels then drift apart along flat valleys), so the run is
-compared on well-determined outputs -- the image series, the fitted model
-TACs and the Poisson log-likelihood -- against the envelope of the oracle's
-own sensitivity: tests/golden/pr1_chaos_envelope.json holds how far the FP64
-oracle run moves when the count calibration is perturbed by 1e-5 (relative),
-and the float32 run must stay within twice that.  The fraction of voxels whose
-maps left the 1e-3 band is reported.
+the image tolerance (1e-4 relative L2).  (2) End to end over 5 iterations, at
+weights where the alternation is stable at PR1's count level (the oracle's own
+run moves by ~1e-5 under a 1e-5 change of the count calibration;
+tests/golden/pr1_chaos_envelope.json): the image series and the model TACs
+within 1e-3 relative L2 of the oracle, the log-likelihood within 1e-5, and
+the share of voxels whose maps leave the 1e-3 band bounded by the oracle's own
+under that perturbation plus 2 %.  (At the weight beta_kp = 0.1 of the config text the
+direct methods are unstable at these counts: a 1e-5 change of the count
+calibration moves the oracle's image by 3 %, so no end-to-end tolerance there
+says anything; that weight is covered teacher-forced.)
 """
 import json
 import os
@@ -24,7 +24,7 @@ import kcs_synth as S
 from oracle import icm as OI
 from oracle import kinetics as OK
 from oracle import osl as OO
-from cases import pr1_problem, problem, rel_l2
+from cases import FLOOR, pr1_problem, problem, rel_l2
 
 pytestmark = pytest.mark.gpu
 
@@ -63,46 +63,80 @@ def test_pr1_osl_pass_with_prior_teacher_forced(cuda_ok, name):
     assert rel_l2(xg.cpu().numpy(), xr) < 1e-4
 
 
-def test_pr1_icm_end_to_end(cuda_ok):
+STABLE = dict(beta_kp=0.01, beta_h=1e4, delta=0.01)
+
+
+def _envelope(section):
+    with open(os.path.join(os.path.dirname(__file__), "golden", "pr1_chaos_envelope.json")) as f:
+        return json.load(f)[section]
+
+
+def _icm_pair(method, weights):
+    """5 ICM iterations x 10 LM steps of the CUDA path and of the oracle on PR1."""
     K, P, W, kg, kin = _setup()
     dt = _f32(P["dt"])
     kappa = float(np.float32(P["kappa"]))
     counts = _t(P["counts"])
     x = K.init_image(kg, _t(dt), kappa, counts)
     params = _t(np.broadcast_to(np.array(S.XI0)[:, None, None, None], (4, 1, W.ny, W.nx)))
-    st = K.Study(kg, kin, _t(dt), kappa, counts, x, params, n_lm=10, beta_kp=0.1, beta_h=0.1,
-                 delta=0.01)
+    st = K.Study(kg, kin, _t(dt), kappa, counts, x, params, n_lm=10, method=method, **weights)
     lls = []
     for _ in range(5):
         st.iterate(1)
         lls.append(st.loglik().item())
     torch.cuda.synchronize()
     assert st.iterations == 5
-    print("PR1 ICM log-likelihood per iteration:", " ".join(f"{v:.6e}" for v in lls))
-    xr, xir, kir, Fr = OI.icm(P["g"], P["counts"], kappa, P["ts"], P["te"], S.FENG, 5, 10,
-                              0.1, 0.1, 0.01)
-    assert abs(lls[-1] / OO.loglik(P["g"], x.double().cpu().numpy(), P["counts"], kappa, dt)
-               - 1) < 1e-5
-    xg = x.double().cpu().numpy()
-    xi_g = params.double().cpu().numpy()
-    e_img = rel_l2(xg, xr)
-    e_F = rel_l2(st.F.cpu().numpy(), Fr)
-    floor = 1e-2 * np.array([0.06, 0.10, 0.04, 0.03])[:, None, None, None]
-    off = np.any(np.abs(xi_g - xir) > 1e-3 * np.maximum(np.abs(xir), floor), axis=0)
-    lab = S.labels_pr1()
-    ki_g = OK.ki(xi_g)[0]
+    ref = OI.icm(P["g"], P["counts"], kappa, P["ts"], P["te"], S.FENG, 5, 10,
+                 weights["beta_kp"], weights["beta_h"], weights["delta"], method=method)
+    got = (x.double().cpu().numpy(), params.double().cpu().numpy(), st.F.double().cpu().numpy())
+    return P, dt, kappa, lls, got, ref
+
+
+@pytest.mark.parametrize("method", ["kcs", "direct"])
+def test_pr1_icm_end_to_end(cuda_ok, method):
+    """5 ICM iterations on PR1 at weights where the alternation is stable at
+    its count level (beta_kp = 0.01, beta_h = 1e4, delta = 0.01; the FP64
+    oracle's own run moves by ~1e-5 when kappa moves by 1e-5, see
+    tests/golden/pr1_chaos_envelope.json "stable"): the image series and the
+    model TACs within 1e-3 relative L2 of the oracle's; the share of voxels
+    whose maps leave the 1e-3 band (LM decisions that went the other way in
+    float32 somewhere along the trajectory, then different valleys) at most
+    that of the oracle's own run under a 1e-5 change of kappa plus 2 % of the
+    voxels: a guard against a regression, not the map parity, which the
+    teacher-forced LM tests establish per voxel.  KCS against DIRECT (no Huber
+    term) shows the Huber weight moves the maps far more than the float32
+    differences."""
+    P, dt, kappa, lls, (xg, xi_g, Fg), (xr, xir, kir, Fr) = _icm_pair(method, STABLE)
+    env = _envelope("stable" if method == "kcs" else "stable_direct")["kappa_rel_1e-05"]
+    print(f"PR1 {method} ICM log-likelihood per iteration:", " ".join(f"{v:.6e}" for v in lls))
+    assert abs(lls[-1] / OO.loglik(P["g"], xg, P["counts"], kappa, dt) - 1) < 1e-5
+    e_img, e_F = rel_l2(xg, xr), rel_l2(Fg, Fr)
+    off = np.any(np.abs(xi_g - xir) > 1e-3 * np.maximum(np.abs(xir), FLOOR[:, None, None, None]),
+                 axis=0)
     ll_g = OO.loglik(P["g"], xg, P["counts"], kappa, dt)
     ll_r = OO.loglik(P["g"], xr, P["counts"], kappa, dt)
-    ki_dev = max(abs(ki_g[lab == c].mean() / kir[0][lab == c].mean() - 1) for c in (1, 2, 3))
-    env = json.load(open(os.path.join(os.path.dirname(__file__), "golden",
-                                      "pr1_chaos_envelope.json")))
-    print(f"PR1 ICM x5: image rel-L2 {e_img:.2e} (oracle envelope {env['image_rel_l2']:.2e}), "
-          f"model-TAC rel-L2 {e_F:.2e} ({env['model_tac_rel_l2']:.2e}), loglik rel diff "
-          f"{abs(ll_g / ll_r - 1):.2e} ({env['loglik_rel']:.2e}), class-mean Ki rel diff "
-          f"{ki_dev:.2e}, voxels outside the 1e-3 map band {off.mean():.1%}")
-    assert e_img < 2 * env["image_rel_l2"]
-    assert e_F < 2 * env["model_tac_rel_l2"]
-    assert abs(ll_g / ll_r - 1) < 2 * env["loglik_rel"]
+    print(f"PR1 {method} x5 (beta_kp 0.01, beta_h 1e4): image rel-L2 {e_img:.2e} (oracle "
+          f"under kappa x (1 +- 1e-5): {env['image_rel_l2']:.2e}), model-TAC rel-L2 {e_F:.2e} "
+          f"({env['model_tac_rel_l2']:.2e}), loglik rel diff {abs(ll_g / ll_r - 1):.2e}, "
+          f"voxels outside the 1e-3 map band {off.mean():.2%} "
+          f"({env['map_voxels_outside_1e-3']:.2%})")
+    assert e_img <= 1e-3
+    assert e_F <= 1e-3
+    assert abs(ll_g / ll_r - 1) <= 1e-5
+    assert off.mean() <= env["map_voxels_outside_1e-3"] + 0.02
+    if method == "kcs":
+        # the same run without the Huber term (DIRECT) on the GPU
+        K, _, W, kg, kin = _setup()
+        counts = _t(P["counts"])
+        x = K.init_image(kg, _t(dt), kappa, counts)
+        params = _t(np.broadcast_to(np.array(S.XI0)[:, None, None, None], (4, 1, W.ny, W.nx)))
+        K.Study(kg, kin, _t(dt), kappa, counts, x, params, n_lm=10, method="direct",
+                **STABLE).iterate(5)
+        torch.cuda.synchronize()
+        d_huber = rel_l2(params.double().cpu().numpy(), xi_g)
+        print(f"maps with beta_h = 1e4 vs without the Huber term: rel-L2 {d_huber:.2e}; GPU vs "
+              f"oracle {rel_l2(xi_g, xir):.2e}")
+        assert d_huber > 10 * rel_l2(xi_g, xir)
 
 
 def test_pr1_graph_replay_identical_and_timed(cuda_ok):
@@ -131,49 +165,32 @@ def test_pr1_graph_replay_identical_and_timed(cuda_ok):
         assert np.array_equal(u, v)
 
 
-@pytest.mark.parametrize("method", ["indirect", "direct"])
-def test_pr1_other_methods_end_to_end(cuda_ok, method):
-    """INDIRECT (OSEM then one post-reconstruction fit) and DIRECT (no spatial
-    prior in the fit) against the oracle's same method (Sec. IV-A).  The OSEM
-    image of INDIRECT is deterministic and contractive, so it is held to the
-    image tolerance; the fitted outputs are compared with the oracle's own
-    sensitivity envelope for that method."""
+def test_pr1_indirect_end_to_end(cuda_ok):
+    """INDIRECT (Sec. IV-A): 5 OSEM passes (no prior, no fit), then one
+    post-reconstruction fit of 10 LM steps without the spatial prior.  OSEM is
+    deterministic and contractive, so its image is held to the image
+    tolerance; the post-fit model TACs to 1e-3 relative L2."""
     K, P, W, kg, kin = _setup()
     dt = _f32(P["dt"])
     kappa = float(np.float32(P["kappa"]))
     counts = _t(P["counts"])
     x = K.init_image(kg, _t(dt), kappa, counts)
-    params = _t(np.broadcast_to(np.array(S.XI0)[:, None, None, None], (4, 1, W.ny, W.nx)))
+    start = _t(np.broadcast_to(np.array(S.XI0)[:, None, None, None], (4, 1, W.ny, W.nx)))
+    params = start.clone()
     st = K.Study(kg, kin, _t(dt), kappa, counts, x, params, n_lm=10, beta_kp=0.1, beta_h=0.1,
-                 delta=0.01, method=method)
+                 delta=0.01, method="indirect")
     st.iterate(5)
-    if method == "indirect":
-        torch.cuda.synchronize()
-        x_osem = x.double().cpu().numpy()
-        assert np.array_equal(params.cpu().numpy(), _t(np.broadcast_to(
-            np.array(S.XI0)[:, None, None, None], (4, 1, W.ny, W.nx))).cpu().numpy())
-        st.fit(10)
+    torch.cuda.synchronize()
+    x_osem = x.double().cpu().numpy()
+    assert torch.equal(params, start)            # no fit during the OSEM passes
+    st.fit(10)
     torch.cuda.synchronize()
     xr, xir, kir, Fr = OI.icm(P["g"], P["counts"], kappa, P["ts"], P["te"], S.FENG, 5, 10,
-                              0.1, 0.1, 0.01, method=method)
-    env = json.load(open(os.path.join(os.path.dirname(__file__), "golden",
-                                      "pr1_chaos_envelope.json")))["methods"][method]
-    xg = x.double().cpu().numpy()
-    e_img, e_F = rel_l2(xg, xr), rel_l2(st.F.cpu().numpy(), Fr)
-    lab = S.labels_pr1()
-    ki_g = OK.ki(params.double().cpu().numpy())[0]
-    ki_dev = max(abs(ki_g[lab == c].mean() / kir[0][lab == c].mean() - 1) for c in (1, 2, 3))
-    print(f"PR1 {method} x5: image rel-L2 {e_img:.2e} (envelope {env['image_rel_l2']:.2e}), "
-          f"model-TAC rel-L2 {e_F:.2e} ({env['model_tac_rel_l2']:.2e}), class-mean Ki rel diff "
-          f"{ki_dev:.2e}")
-    if method == "indirect":
-        assert rel_l2(x_osem, xr) < 1e-4
-    else:
-        assert e_img < 2 * env["image_rel_l2"] + 1e-4
-    # float32 and float64 LM decisions differ on flat-valley voxels even from the
-    # same image, so the fitted model TACs get a float32 allowance of 5e-3
-    assert e_F < 2 * env["model_tac_rel_l2"] + 5e-3
-    assert ki_dev < 2 * env["Ki_class_mean_rel"] + 0.01
+                              0.1, 0.1, 0.01, method="indirect")
+    e_img, e_F = rel_l2(x_osem, xr), rel_l2(st.F.cpu().numpy(), Fr)
+    print(f"PR1 indirect x5: OSEM image rel-L2 {e_img:.2e}, post-fit model-TAC rel-L2 {e_F:.2e}")
+    assert e_img < 1e-4
+    assert e_F < 1e-3
 
 
 def test_stacked_planes_equal_separate_studies(cuda_ok):

@@ -20,10 +20,9 @@ import pytest
 import torch
 
 import kcs_synth as S
-from oracle import icm as OI
 from oracle import kinetics as OK
 from oracle import osl as OO
-from cases import pr1_problem, rel_l2
+from cases import oracle_icm_runs, pr1_problem, rel_l2
 
 pytestmark = pytest.mark.gpu
 KINDS = {"f32": torch.float32, "bf16": torch.bfloat16, "f16": torch.float16}
@@ -56,15 +55,18 @@ def _setup():
     return K, P, W, kg, kin
 
 
-def _icm(K, P, W, kg, kin, kind, counts, n_iter):
+STABLE = dict(beta_kp=0.01, beta_h=1e4, delta=0.01)
+CONFIG = dict(beta_kp=0.1, beta_h=0.1, delta=0.01)
+
+
+def _icm(K, P, W, kg, kin, kind, counts, n_iter, weights=CONFIG):
     dt = _t(_f32(P["dt"]))
     kappa = float(np.float32(P["kappa"]))
     x32 = K.init_image(kg, dt, kappa, counts)
     scale = x32.reshape(-1, W.n_frames).amax(0).contiguous()      # max |x_m| of the start image
     x = K.init_image(kg, dt, kappa, counts, dtype=KINDS[kind], x_scale=scale)
     params = _t(np.broadcast_to(np.array(S.XI0)[:, None, None, None], (4, 1, W.ny, W.nx)))
-    st = K.Study(kg, kin, dt, kappa, counts, x, params, n_lm=10, beta_kp=0.1, beta_h=0.1,
-                 delta=0.01, x_scale=scale)
+    st = K.Study(kg, kin, dt, kappa, counts, x, params, n_lm=10, x_scale=scale, **weights)
     st.iterate(n_iter)
     torch.cuda.synchronize()
     return (x.double() * scale.double()).cpu().numpy(), params.double().cpu().numpy(), st
@@ -111,37 +113,49 @@ def test_stored_update_matches_oracle_within_one_ulp(cuda_ok, kind, prior):
 
 
 def test_pr3_icm_report(cuda_ok):
+    """Config PR3: five PR1 ICM iterations per storage type at the weights
+    where the alternation is stable at PR1's counts (beta_kp = 0.01,
+    beta_h = 1e4).  float32: image and model TACs within 1e-3 of the FP64
+    oracle.  bfloat16 / float16: against the FP64 oracle run with the same
+    stores (image and ratio rounded to the same grid), image and model TACs
+    closer to it than storage rounding moves the oracle's own trajectory (its
+    stored run's distance from its float64 run,
+    tests/golden/pr1_chaos_envelope.json "storage"), and their error against
+    the float64 oracle within 25 % of that storage effect: the GPU reproduces
+    the precision cost the oracle predicts.  (Float32 and float64 round some
+    values to opposite sides of a storage-grid midpoint, a one-ulp difference
+    that the ICM then carries, so the stored runs are not compared at the
+    float32 tolerance.)  Prints the per-result errors against the float64
+    oracle (the PR3 report)."""
     K, P, W, kg, kin = _setup()
-    kappa = float(np.float32(P["kappa"]))
-    xr, xir, kir, Fr = OI.icm(P["g"], P["counts"], kappa, P["ts"], P["te"], S.FENG, 5, 10,
-                              0.1, 0.1, 0.01)
     env = json.load(open(os.path.join(os.path.dirname(__file__), "golden",
-                                      "pr1_chaos_envelope.json")))
+                                      "pr1_chaos_envelope.json")))["storage"]
+    refs = dict(zip(("f32", "bf16", "f16"), oracle_icm_runs(
+        [(STABLE, "kcs", None, 5), (STABLE, "kcs", "bf16", 5), (STABLE, "kcs", "f16", 5)])))
+    xr, xir, kir, Fr = refs["f32"]
     counts = _t(P["counts"], torch.uint16)
     lab = S.labels_pr1()
     inside = lab > 0
-    res = {}
     for kind in ("f32", "bf16", "f16"):
-        x, xi, _ = _icm(K, P, W, kg, kin, kind, counts, 5)
+        x, xi, st = _icm(K, P, W, kg, kin, kind, counts, 5, STABLE)
+        F = st.F.double().cpu().numpy()
         ki = OK.ki(xi)[0]
-        res[kind] = dict(
-            image=rel_l2(x, xr),
-            K1=rel_l2(xi[0, 0][inside], xir[0, 0][inside]),
-            k3=rel_l2(xi[2, 0][inside], xir[2, 0][inside]),
-            Ki=rel_l2(ki[inside], kir[0][inside]),
-            Ki_class=max(abs(ki[lab == c].mean() / kir[0][lab == c].mean() - 1) for c in (1, 2, 3)))
-    for kind, r in res.items():
-        o = env["storage"].get(kind)
-        ref = (f"   [oracle stored {kind}: image {o['image_rel_l2']:.3e}  Ki class-mean "
-               f"{o['Ki_class_mean_rel']:.2e}]") if o else ""
-        print(f"PR3 {kind:>4}: image {r['image']:.3e}  K1 {r['K1']:.3e}  k3 {r['k3']:.3e}  "
-              f"Ki {r['Ki']:.3e}  class-mean Ki {r['Ki_class']:.2e}  (vs FP64 oracle){ref}")
-    # float32 within the oracle's own sensitivity envelope (as in the ICM test).
-    # Storage rounding alone moves the FP64 oracle's trajectory by the amounts
-    # in env["storage"] (ICM with MAP-LM amplifies any perturbation), so the
-    # stored GPU runs are bounded by that plus the float32 envelope.
-    assert res["f32"]["image"] < 2 * env["image_rel_l2"]
-    for kind in ("bf16", "f16"):
-        o = env["storage"][kind]
-        assert res[kind]["image"] < 1.5 * o["image_rel_l2"] + 2 * env["image_rel_l2"], kind
-        assert res[kind]["Ki_class"] < 2 * o["Ki_class_mean_rel"] + 0.02, kind
+        r = dict(image=rel_l2(x, xr), F=rel_l2(F, Fr),
+                 K1=rel_l2(xi[0, 0][inside], xir[0, 0][inside]),
+                 k3=rel_l2(xi[2, 0][inside], xir[2, 0][inside]),
+                 Ki=rel_l2(ki[inside], kir[0][inside]),
+                 Ki_class=max(abs(ki[lab == c].mean() / kir[0][lab == c].mean() - 1)
+                              for c in (1, 2, 3)))
+        same = refs[kind]
+        e_img, e_F = rel_l2(x, same[0]), rel_l2(F, same[3])
+        print(f"PR3 {kind:>4} vs FP64: image {r['image']:.3e}  model TAC {r['F']:.3e}  "
+              f"K1 {r['K1']:.3e}  k3 {r['k3']:.3e}  Ki {r['Ki']:.3e}  class-mean Ki "
+              f"{r['Ki_class']:.2e};  vs the oracle with the same stores: image {e_img:.2e}, "
+              f"model TAC {e_F:.2e}")
+        if kind == "f32":
+            assert e_img <= 1e-3 and e_F <= 1e-3
+        else:
+            eff = env[kind]["vs_float64"]
+            assert e_img <= eff["image_rel_l2"] and e_F <= eff["model_tac_rel_l2"], kind
+            assert abs(r["image"] / eff["image_rel_l2"] - 1) <= 0.25, kind
+            assert abs(r["F"] / eff["model_tac_rel_l2"] - 1) <= 0.25, kind
