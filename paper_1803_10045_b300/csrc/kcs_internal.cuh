@@ -71,6 +71,8 @@ struct __align__(16) AngleTab {
   float tc;        // (n_major - 1) / 2: centre of the major axis
   float centre;    // (n_minor - 1) / 2: centre of the minor axis
   float rband;     // |1 / beta| + 1e-3: half-width in bins of the candidates of a voxel
+  int pair;        // 1: at most two consecutive bins reach any voxel (see kcs_create_geometry)
+  int pad_[3];
 };
 
 }  // namespace kcs
@@ -84,6 +86,7 @@ struct kcs_geometry {
   std::vector<int> h_angles;
   std::vector<int> off;   // off[k] .. off[k+1]: angles of subset k
   int max_sub;
+  int pair_all;           // every angle obeys the pair rule of the back-projection
 };
 
 namespace kcs {

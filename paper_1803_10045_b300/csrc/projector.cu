@@ -123,6 +123,7 @@ struct ProjArgs {
   const float4* F;          // model TACs or null
   float prior_scale;        // beta / (S sigma2)
   double* ll_partial;       // non-null: accumulate the log-likelihood, no ratio
+  int pair_all;             // every angle obeys the pair rule (AngleTab::pair)
 };
 
 constexpr int LL_PARTS = 1024;   // partial sums of the log-likelihood
@@ -232,10 +233,10 @@ __global__ void __launch_bounds__(FWD_THREADS) k_forward(ProjArgs p) {
     atomicAdd(p.ll_partial + (blockIdx.x & (LL_PARTS - 1)), (double)t);
     return;
   }
-  rho.x = yb.x > 0.f ? s.x / yb.x : 0.f;
-  rho.y = yb.y > 0.f ? s.y / yb.y : 0.f;
-  rho.z = yb.z > 0.f ? s.z / yb.z : 0.f;
-  rho.w = yb.w > 0.f ? s.w / yb.w : 0.f;
+  rho.x = yb.x > 0.f ? __fdividef(s.x, yb.x) : 0.f;
+  rho.y = yb.y > 0.f ? __fdividef(s.y, yb.y) : 0.f;
+  rho.z = yb.z > 0.f ? __fdividef(s.z, yb.z) : 0.f;
+  rho.w = yb.w > 0.f ? __fdividef(s.w, yb.w) : 0.f;
   st4(static_cast<TY*>(p.yout) + oi * 4, rho);
 }
 
@@ -412,10 +413,10 @@ __global__ void __launch_bounds__(BK_TILE * BK_TILE) k_back_tiled(ProjArgs p, in
       den.z = fmaxf(fmaf(ps, xv.z - Fv.z, den.z), 1e-3f * den.z);
       den.w = fmaxf(fmaf(ps, xv.w - Fv.w, den.w), 1e-3f * den.w);
     }
-    xv.x = xv.x * (p.kappa * dt.x * acc[q].x) / den.x;
-    xv.y = xv.y * (p.kappa * dt.y * acc[q].y) / den.y;
-    xv.z = xv.z * (p.kappa * dt.z * acc[q].z) / den.z;
-    xv.w = xv.w * (p.kappa * dt.w * acc[q].w) / den.w;
+    xv.x = __fdividef(xv.x * (p.kappa * dt.x * acc[q].x), den.x);
+    xv.y = __fdividef(xv.y * (p.kappa * dt.y * acc[q].y), den.y);
+    xv.z = __fdividef(xv.z * (p.kappa * dt.z * acc[q].z), den.z);
+    xv.w = __fdividef(xv.w * (p.kappa * dt.w * acc[q].w), den.w);
     if (p.xscale) xv = make_float4(xv.x / sc.x, xv.y / sc.y, xv.z / sc.z, xv.w / sc.w);
     st4(static_cast<TX*>(p.xout) + (vi + q) * 4, xv);
   }
@@ -490,8 +491,8 @@ __global__ void k_selftest_wait(int limit) {
 // for the angle it is about to use, so the copies of later angles overlap the
 // work on earlier ones and no thread spends issue slots on staging.  Rows are
 // dense in shared memory (pitch = one bin's frames).
-template <int MQ, int MODE, class TX, class TY>
-__global__ void __launch_bounds__(BK_TILE * BK_TILE) k_back_bulk(ProjArgs p, int rows_max,
+template <int MQ, int MODE, class TX, class TY, bool PAIR>
+__global__ void __launch_bounds__(BK_TILE * BK_TILE, 4) k_back_bulk(ProjArgs p, int rows_max,
                                                                   int achunk) {
   // bytes of one bin row: p.yq quads, a multiple of 16 (checked by the launcher)
   const int RB = p.yq * 4 * (int)sizeof(TY);
@@ -583,10 +584,44 @@ __global__ void __launch_bounds__(BK_TILE * BK_TILE) k_back_bulk(ProjArgs p, int
       // meets minor index m; the exact test below decides
       const float u = fmaf((float)m - inner, T.inv_beta, bc);
       const int lo = s_lo[c];
-      const int b_lo = max((int)ceilf(u - T.rband), lo);
-      const int b_hi = min((int)floorf(u + T.rband), lo + s_cnt[c] - 1);
       const TY* rows = reinterpret_cast<const TY*>(sraw + (size_t)c * rows_max * RB);
       const size_t binrow = (size_t)(z * p.A + a) * p.B;
+      if (MODE == 1 && PAIR) {
+        // At most two consecutive bins reach this voxel: the last whose sample
+        // lies below m and the first at or above it.  The pair is fixed by
+        // one exact test of the forward's own position at the bin nearest
+        // the real crossing u, so it holds whatever the rounding of u; both
+        // candidates are then processed without a loop or a branch, in
+        // ascending bin order as the forward's triples are summed (a zero
+        // weight adds exactly nothing: the staged ratios are finite).
+        const int cnt = s_cnt[c];
+        if (cnt == 0) continue;                            // no staged row reaches the tile
+        const float mf = (float)m;
+        const float kf = rintf(u);
+        const float frk = minor_pos(kf - bc, T.beta, inner);
+        const bool below = (frk >= mf) == (T.beta > 0.f);    // pair {k - 1, k}
+        const float fro = minor_pos((below ? kf - 1.f : kf + 1.f) - bc, T.beta, inner);
+        const int b0 = (int)kf - (below ? 1 : 0);
+        float frs[2] = {below ? fro : frk, below ? frk : fro};
+#pragma unroll
+        for (int e = 0; e < 2; ++e) {
+          const int r = b0 + e - lo;                     // staged row of the candidate
+          const float fr = frs[e];
+          const float fl = floorf(fr);
+          const int jj = (int)fl;
+          const float f = fr - fl;
+          float wt = (jj == m) ? 1.0f - f : ((jj + 1 == m) ? f : 0.0f);
+          wt = ((unsigned)r < (unsigned)cnt) ? wt * T.w : 0.0f;
+          if (p.bin_factor && wt != 0.0f) wt *= __ldg(p.bin_factor + binrow + b0 + e);
+          const TY* row = rows + (size_t)min(max(r, 0), cnt - 1) * p.yq * 4;
+#pragma unroll
+          for (int q = 0; q < MQ; ++q) fma4(acc[q], wt, ld4(row + q * 4));
+          sens += wt;
+        }
+        continue;
+      }
+      const int b_lo = max((int)ceilf(u - T.rband), lo);
+      const int b_hi = min((int)floorf(u + T.rband), lo + s_cnt[c] - 1);
       for (int b = b_lo; b <= b_hi; ++b) {
         const float fr = minor_pos((float)b - bc, T.beta, inner);
         const float fl = floorf(fr);
@@ -636,10 +671,10 @@ __global__ void __launch_bounds__(BK_TILE * BK_TILE) k_back_bulk(ProjArgs p, int
       den.z = fmaxf(fmaf(ps, xv.z - Fv.z, den.z), 1e-3f * den.z);
       den.w = fmaxf(fmaf(ps, xv.w - Fv.w, den.w), 1e-3f * den.w);
     }
-    xv.x = xv.x * (p.kappa * dt.x * acc[q].x) / den.x;
-    xv.y = xv.y * (p.kappa * dt.y * acc[q].y) / den.y;
-    xv.z = xv.z * (p.kappa * dt.z * acc[q].z) / den.z;
-    xv.w = xv.w * (p.kappa * dt.w * acc[q].w) / den.w;
+    xv.x = __fdividef(xv.x * (p.kappa * dt.x * acc[q].x), den.x);
+    xv.y = __fdividef(xv.y * (p.kappa * dt.y * acc[q].y), den.y);
+    xv.z = __fdividef(xv.z * (p.kappa * dt.z * acc[q].z), den.z);
+    xv.w = __fdividef(xv.w * (p.kappa * dt.w * acc[q].w), den.w);
     if (p.xscale) xv = make_float4(xv.x / sc.x, xv.y / sc.y, xv.z / sc.z, xv.w / sc.w);
     st4(static_cast<TX*>(p.xout) + (vi + q) * 4, xv);
   }
@@ -755,6 +790,7 @@ static int rho_pitch(int MQ, int x_type) { return x_type == KCS_F32 ? (MQ | 1) :
 
 static ProjArgs base_args(const kcs_geometry* g, int subset) {
   ProjArgs p{};
+  p.pair_all = g->pair_all;
   p.ang = g->d_ang;
   p.sub = subset_dev(g, subset);
   p.n_sub = subset_count(g, subset);
@@ -825,12 +861,14 @@ static int launch_back_mq(const ProjArgs& p0, int rows_max, cudaStream_t s) {
     const int achunk = (int)std::min<size_t>(BK_ACHUNK, BK_SMEM_MAX / row_bytes);
     KCS_REQUIRE(achunk >= 1, "bins are too fine relative to voxels for the tiled back-projection");
     const size_t smem = row_bytes * achunk;
-    KCS_CUDA(cudaFuncSetAttribute(k_back_bulk<MQ, MODE, TX, TY>,
-                                  cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     const long long tiles = (long long)((p.nx + BK_TILE - 1) / BK_TILE) *
                             ((p.ny + BK_TILE - 1) / BK_TILE) * p.nz;
-    k_back_bulk<MQ, MODE, TX, TY><<<(unsigned)tiles, BK_TILE * BK_TILE, smem, s>>>(p, rows_max,
-                                                                                 achunk);
+    // the OSL update with every angle under the pair rule takes the
+    // two-candidate instance; everything else the general candidate loop
+    auto kern = (MODE == 1 && p.pair_all) ? k_back_bulk<MQ, MODE, TX, TY, true>
+                                          : k_back_bulk<MQ, MODE, TX, TY, false>;
+    KCS_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    kern<<<(unsigned)tiles, BK_TILE * BK_TILE, smem, s>>>(p, rows_max, achunk);
     return KCS_OK;
   }
   const size_t row_bytes = sizeof(float4) * rows_max * bk_pitch(MQ);
@@ -913,11 +951,32 @@ int kcs_create_geometry(kcs_geometry_t** out, int nx, int ny, int nz, float vox_
     T.tc = 0.5f * (float)(n_major - 1);      // the kernels' own float expressions
     T.centre = 0.5f * (float)(n_minor - 1);
     T.rband = fabsf(T.inv_beta) + 1e-3f;
+    // Pair rule: a voxel at minor index m receives weight from the rays whose
+    // sample lies in (m - 1, m + 1).  Consecutive bins' samples are |beta|
+    // apart before rounding and each is rounded once (one fused multiply-add,
+    // error <= half an ulp of |fr| < n_minor + 1), so when |beta| - 1 exceeds
+    // one such ulp at most two samples fit in that open interval, on
+    // consecutive bins.  |beta| = 1 with an inner position that is exactly the
+    // minor centre for every major step (|gamma| (n_major - 1) / 2 below a
+    // quarter ulp of the centre) makes every sample position an exact
+    // half-integer sum, with the same conclusion.
+    {
+      const float lim = (float)(n_minor + 1);
+      const float ulp = nextafterf(lim, 2.f * lim) - lim;
+      const float ab = fabsf(T.beta);
+      const float cen_ulp = nextafterf(T.centre + 1.f, 1e30f) - (T.centre + 1.f);
+      const bool exact1 = ab == 1.f && fabsf(T.gamma) * (0.5f * (float)n_major) < 0.25f * cen_ulp;
+      T.pair = (ab - 1.f > ulp || exact1) ? 1 : 0;
+    }
+    T.pad_[0] = T.pad_[1] = T.pad_[2] = 0;
     tab[a] = T;
   }
+  int pair_all = 1;
+  for (const AngleTab& T : tab) pair_all &= T.pair;
   kcs_geometry* g = new kcs_geometry();
   g->nx = nx; g->ny = ny; g->nz = nz; g->B = n_bins; g->A = n_angles; g->S = n_subsets;
   g->vox = vox_mm; g->bin = bin_mm;
+  g->pair_all = pair_all;
   cudaGetDevice(&g->device);
   g->off.assign(n_subsets + 1, 0);
   for (int k = 0; k < n_subsets; ++k) {
