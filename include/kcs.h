@@ -91,6 +91,11 @@ int kcs_version(void);
  * Allocates a small per-angle table on the current device. */
 int kcs_create_geometry(kcs_geometry_t** out, int nx, int ny, int nz, float vox_mm,
                         int n_bins, int n_angles, float bin_mm, int n_subsets);
+/* The same, with the per-angle table uploaded asynchronously on stream: the
+ * geometry is ready for work issued later on that stream (or after the stream
+ * has been synchronised); kcs_create_geometry waits for the upload. */
+int kcs_create_geometry_ex(kcs_geometry_t** out, int nx, int ny, int nz, float vox_mm,
+                           int n_bins, int n_angles, float bin_mm, int n_subsets, void* stream);
 int kcs_destroy_geometry(kcs_geometry_t* g);
 /* Host copy of the angle indices of subset k (subset = -1: all angles).
  * angles_out may be NULL to query the count only. */
@@ -107,6 +112,18 @@ int kcs_forward_project(const kcs_geometry_t* g, int subset, int n_frames,
  * x [Z][ny][nx][M] (overwritten). */
 int kcs_back_project(const kcs_geometry_t* g, int subset, int n_frames,
                      const float* y, float* x, void* stream);
+/* Precision form of the two calls above (Eq. 2's sums over stored data):
+ * kcs_forward_project_ex projects an image stored as x_type (KCS_F32,
+ * KCS_BF16, KCS_F16) holding x / x_scale[m] (x_scale [M] device, NULL = 1),
+ * accumulating in float32: y = P_k (x_scale * x) as float32.
+ * kcs_back_project_ex back-projects a sinogram stored as y_type holding
+ * y / y_scale[m]: x = P_k^T (y_scale * y) as float32, the exact transpose of
+ * kcs_forward_project_ex.  16-bit arrays must be 8-byte aligned.  With KCS_F32
+ * and NULL scales both equal the plain calls bit for bit. */
+int kcs_forward_project_ex(const kcs_geometry_t* g, int subset, int n_frames, const void* x,
+                           int x_type, const float* x_scale, float* y, void* stream);
+int kcs_back_project_ex(const kcs_geometry_t* g, int subset, int n_frames, const void* y,
+                        int y_type, const float* y_scale, float* x, void* stream);
 /* sens = sum_{d in S_k} n_d p_vd per voxel [Z][ny][nx] (bin_factor NULL: n_d = 1). */
 int kcs_sensitivity(const kcs_geometry_t* g, int subset, const float* bin_factor,
                     float* sens, void* stream);

@@ -299,7 +299,10 @@ def float32_spread(x, maps, lam, t_start, t_end, feng, beta, delta, nbhd="2d", t
     dev_trial [V][4]: largest |trial_f - trial| over the recomputations,
     dev_margin [V]: largest |m_f - m| of the decision margin
     m = Phi(trial) - Phi + tau Phi, flip [V]: some recomputation decides
-    accept/reject differently) with the float64 parts of step_parts()."""
+    accept/reject differently, model_margin [V]: max|F| sum|r| + max|Ft| sum|rt|,
+    the first-order change of the margin per unit relative error of the model
+    values, huber_margin [V]: 2 n beta (H + Ht), its change per unit rounding
+    of the n-term Huber sums) with the float64 parts of step_parts()."""
     f = dtype
     s = step_parts(x, maps, lam, t_start, t_end, feng, beta, delta, lo, hi, nbhd, tau)
     M = x.shape[-1]
@@ -337,21 +340,32 @@ def float32_spread(x, maps, lam, t_start, t_end, feng, beta, delta, nbhd="2d", t
         dev_t = np.maximum(dev_t, np.abs(trial - s["trial"]))
         dev_m = np.maximum(dev_m, np.abs(m_f - margin))
         flip |= (m_f < 0) != s["acc"]
-    s.update(dev_trial=dev_t, dev_margin=dev_m, flip=flip, margin=margin)
+    n_nb = len(NEIGHBOURS) if nbhd == "2d" else len(NEIGHBOURS_3D)
+    Ht_all = huber_local(s["trial_maps"], maps, delta, nbhd).ravel()
+    model_margin = (np.abs(s["F"]).max(axis=1) * np.abs(s["r"]).sum(axis=1)
+                    + np.abs(s["Ft"]).max(axis=1) * np.abs(s["rt"]).sum(axis=1))
+    s.update(dev_trial=dev_t, dev_margin=dev_m, flip=flip, margin=margin,
+             model_margin=model_margin, huber_margin=2 * n_nb * beta * (H + Ht_all))
     return s
 
 
-def strict_voxels(spread, ref_maps, floor, rel_tol=1e-3, share=0.25, margin_factor=4.0):
+def strict_voxels(spread, ref_maps, floor, rel_tol=1e-3, share=0.25, margin_factor=4.0,
+                  model_eps=1e-6):
     """Voxels whose step float32 arithmetic resolves well inside the parity
     tolerance, from a float32_spread() result: no recomputation flips the
-    decision, the decision margin exceeds margin_factor times its float32
-    spread, every trial parameter moves by at most share x the map tolerance
-    rel_tol max(|trial_p|, floor_p), and a = k2 + k3 of the returned maps is
-    at least 1e-6 (below it k2 and k3 are not identifiable).  Boolean [V]."""
+    decision; the decision margin exceeds margin_factor times the sum of its
+    float32 spread, of what a model evaluated within model_eps of its largest
+    value (relative) can move it by, and of what float32 rounding of the Huber
+    sums can; every trial parameter moves by at most share x the map
+    tolerance rel_tol max(|trial_p|, floor_p); and a = k2 + k3 of the returned
+    maps is at least 1e-6 (below it k2 and k3 are not identifiable).
+    Boolean [V]."""
     tr = spread["trial"]
     tol = rel_tol * np.maximum(np.abs(tr), np.asarray(floor, float)[None, :])
     ok = ~spread["flip"]
-    ok &= np.abs(spread["margin"]) > margin_factor * spread["dev_margin"]
+    need = (spread["dev_margin"] + model_eps * spread["model_margin"]
+            + U32 * spread["huber_margin"])
+    ok &= np.abs(spread["margin"]) > margin_factor * need
     ok &= np.all(spread["dev_trial"] <= share * tol, axis=1)
     ref = ref_maps.reshape(4, -1)
     ok &= (ref[1] + ref[2]) >= 1e-6

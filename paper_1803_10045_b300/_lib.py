@@ -54,6 +54,9 @@ SIGNATURES = {
     "kcs_geometry_subset_angles": (i32, [vp, i32, ip, ip]),
     "kcs_forward_project": (i32, [vp, i32, i32, vp, vp, vp]),
     "kcs_back_project": (i32, [vp, i32, i32, vp, vp, vp]),
+    "kcs_create_geometry_ex": (i32, [pp, i32, i32, i32, f32, i32, i32, f32, i32, vp]),
+    "kcs_forward_project_ex": (i32, [vp, i32, i32, vp, i32, vp, vp, vp]),
+    "kcs_back_project_ex": (i32, [vp, i32, i32, vp, i32, vp, vp, vp]),
     "kcs_sensitivity": (i32, [vp, i32, vp, vp, vp]),
     "kcs_osl_workspace_size": (sz, [vp, i32]),
     "kcs_osl_update": (i32, [vp, i32, i32, vp, f32, vp, vp, i32, vp, vp, f32, f32, vp, vp, sz, vp]),

@@ -56,6 +56,7 @@ class Geometry:
 
     def __init__(self, nx, ny, nz, vox_mm, n_bins, n_angles, bin_mm, n_subsets):
         h = C.c_void_p()
+        # synchronous: the geometry may be used from any stream afterwards
         check(lib.kcs_create_geometry(C.byref(h), nx, ny, nz, vox_mm, n_bins, n_angles, bin_mm,
                                       n_subsets))
         self.handle = h
@@ -91,25 +92,39 @@ class Geometry:
         self.close()
 
 
-def forward_project(g: Geometry, x, subset=-1, out=None):
-    """y = P_k x for every frame: [Z][ny][nx][M] -> [Z][A_k][B][M]."""
+def forward_project(g: Geometry, x, subset=-1, out=None, x_scale=None):
+    """y = P_k x for every frame: [Z][ny][nx][M] -> [Z][A_k][B][M] (float32).
+    x float32, or bfloat16 / float16 holding x / x_scale[m]."""
     M = x.shape[-1]
-    px = _ptr(x, "x", g.image_shape(M))
+    xt = _storage(x, (F32, BF16, F16), "x")
+    px = _ptr(x, "x", g.image_shape(M), dtype=x.dtype)
     if out is None:
         out = torch.empty(g.sino_shape(M, subset), device=x.device, dtype=torch.float32)
     py = _ptr(out, "out", g.sino_shape(M, subset))
-    check(lib.kcs_forward_project(g.handle, subset, M, px, py, _stream()))
+    if xt == F32 and x_scale is None:
+        check(lib.kcs_forward_project(g.handle, subset, M, px, py, _stream()))
+    else:
+        check(lib.kcs_forward_project_ex(g.handle, subset, M, px, xt,
+                                         _ptr(x_scale, "x_scale", (M,), allow_none=True), py,
+                                         _stream()))
     return out
 
 
-def back_project(g: Geometry, y, subset=-1, out=None):
-    """x = P_k^T y for every frame: [Z][A_k][B][M] -> [Z][ny][nx][M]."""
+def back_project(g: Geometry, y, subset=-1, out=None, y_scale=None):
+    """x = P_k^T y for every frame: [Z][A_k][B][M] -> [Z][ny][nx][M] (float32).
+    y float32, or bfloat16 / float16 holding y / y_scale[m]."""
     M = y.shape[-1]
-    py = _ptr(y, "y", g.sino_shape(M, subset))
+    yt = _storage(y, (F32, BF16, F16), "y")
+    py = _ptr(y, "y", g.sino_shape(M, subset), dtype=y.dtype)
     if out is None:
         out = torch.empty(g.image_shape(M), device=y.device, dtype=torch.float32)
     px = _ptr(out, "out", g.image_shape(M))
-    check(lib.kcs_back_project(g.handle, subset, M, py, px, _stream()))
+    if yt == F32 and y_scale is None:
+        check(lib.kcs_back_project(g.handle, subset, M, py, px, _stream()))
+    else:
+        check(lib.kcs_back_project_ex(g.handle, subset, M, py, yt,
+                                      _ptr(y_scale, "y_scale", (M,), allow_none=True), px,
+                                      _stream()))
     return out
 
 

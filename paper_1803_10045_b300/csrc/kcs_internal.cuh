@@ -84,6 +84,7 @@ struct kcs_geometry {
   kcs::AngleTab* d_ang;   // [A]
   int* d_angles;          // subset lists concatenated, then 0..A-1 at offset A
   std::vector<int> h_angles;
+  std::vector<kcs::AngleTab> h_tab;   // host copy of d_ang (source of its asynchronous upload)
   std::vector<int> off;   // off[k] .. off[k+1]: angles of subset k
   int max_sub;
   int pair_all;           // every angle obeys the pair rule of the back-projection

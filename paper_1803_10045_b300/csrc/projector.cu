@@ -124,6 +124,7 @@ struct ProjArgs {
   float prior_scale;        // beta / (S sigma2)
   double* ll_partial;       // non-null: accumulate the log-likelihood, no ratio
   int pair_all;             // every angle obeys the pair rule (AngleTab::pair)
+  const float4* yscale;     // per-frame scale of a stored sinogram (back-projection input) or null
 };
 
 constexpr int LL_PARTS = 1024;   // partial sums of the log-likelihood
@@ -393,7 +394,9 @@ __global__ void __launch_bounds__(BK_TILE * BK_TILE) k_back_tiled(ProjArgs p, in
   const size_t vi = ((size_t)(z * p.ny + j) * p.nx + i) * MQ;
   if (MODE == 0) {
 #pragma unroll
-    for (int q = 0; q < MQ; ++q) st4(static_cast<TX*>(p.xout) + (vi + q) * 4, acc[q]);
+    for (int q = 0; q < MQ; ++q)
+      st4(static_cast<TX*>(p.xout) + (vi + q) * 4,
+          p.yscale ? mul4(acc[q], __ldg(p.yscale + q)) : acc[q]);   // stored sinogram -> value
     return;
   }
   if (!(sens > 0.f)) return;   // x unchanged where no ray of the subset sees the voxel
@@ -651,7 +654,9 @@ __global__ void __launch_bounds__(BK_TILE * BK_TILE, 4) k_back_bulk(ProjArgs p, 
   const size_t vi = ((size_t)(z * p.ny + j) * p.nx + i) * MQ;
   if (MODE == 0) {
 #pragma unroll
-    for (int q = 0; q < MQ; ++q) st4(static_cast<TX*>(p.xout) + (vi + q) * 4, acc[q]);
+    for (int q = 0; q < MQ; ++q)
+      st4(static_cast<TX*>(p.xout) + (vi + q) * 4,
+          p.yscale ? mul4(acc[q], __ldg(p.yscale + q)) : acc[q]);   // stored sinogram -> value
     return;
   }
   if (!(sens > 0.f)) return;   // x unchanged where no ray of the subset sees the voxel
@@ -782,6 +787,10 @@ static int check_geom(const kcs_geometry* g, int subset, int n_frames) {
 }
 
 static bool aligned16(const void* p) { return ((uintptr_t)p & 15u) == 0; }
+// a float array on 16 bytes, a 16-bit one on 8
+static bool aligned_for(const void* ptr, int t) {
+  return ((uintptr_t)ptr & (t == KCS_F32 ? 15u : 7u)) == 0;
+}
 // Quads per bin row of the ratio kept in the OSL workspace: float rows get an
 // odd number of 16-byte quads so that the back-projection's 128-bit reads of
 // up to 8 consecutive bins fall in distinct shared-memory bank groups (a
@@ -822,6 +831,13 @@ static void launch_forward_t(int MQ, const ProjArgs& p0, cudaStream_t s) {
 // Plain forward projection (float image -> float sinogram).
 static void launch_forward(int MQ, const ProjArgs& p, cudaStream_t s) {
   launch_forward_t<false, float, float, float>(MQ, p, s);
+}
+
+// Plain forward projection of an image stored as tx (float sinogram out).
+static void launch_forward_x(int MQ, int tx, const ProjArgs& p, cudaStream_t s) {
+  if (tx == KCS_BF16) launch_forward_t<false, __nv_bfloat16, float, float>(MQ, p, s);
+  else if (tx == KCS_F16) launch_forward_t<false, __half, float, float>(MQ, p, s);
+  else launch_forward_t<false, float, float, float>(MQ, p, s);
 }
 
 // Forward + ratio with a stored image of type tx (the ratio is stored the same
@@ -865,8 +881,9 @@ static int launch_back_mq(const ProjArgs& p0, int rows_max, cudaStream_t s) {
                             ((p.ny + BK_TILE - 1) / BK_TILE) * p.nz;
     // the OSL update with every angle under the pair rule takes the
     // two-candidate instance; everything else the general candidate loop
-    auto kern = (MODE == 1 && p.pair_all) ? k_back_bulk<MQ, MODE, TX, TY, true>
-                                          : k_back_bulk<MQ, MODE, TX, TY, false>;
+    auto kern = k_back_bulk<MQ, MODE, TX, TY, false>;
+    if constexpr (MODE == 1)
+      if (p.pair_all) kern = k_back_bulk<MQ, MODE, TX, TY, true>;
     KCS_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     kern<<<(unsigned)tiles, BK_TILE * BK_TILE, smem, s>>>(p, rows_max, achunk);
     return KCS_OK;
@@ -901,9 +918,14 @@ static int launch_back_t(int MQ, const ProjArgs& p, int rows_max, cudaStream_t s
 
 // MODE 0: float sinogram -> float image.  MODE 1: OSL update of an image stored
 // as tx from a ratio stored the same way.
+// MODE 0: tx is the storage type of the sinogram y (the image out is float).
 template <int MODE>
 static int launch_back(int MQ, int tx, const ProjArgs& p, int rows_max, cudaStream_t s) {
-  if (MODE == 0) return launch_back_t<0, float, float>(MQ, p, rows_max, s);
+  if (MODE == 0) {
+    if (tx == KCS_BF16) return launch_back_t<0, float, __nv_bfloat16>(MQ, p, rows_max, s);
+    if (tx == KCS_F16) return launch_back_t<0, float, __half>(MQ, p, rows_max, s);
+    return launch_back_t<0, float, float>(MQ, p, rows_max, s);
+  }
   if (tx == KCS_BF16) return launch_back_t<MODE, __nv_bfloat16, __nv_bfloat16>(MQ, p, rows_max, s);
   if (tx == KCS_F16) return launch_back_t<MODE, __half, __half>(MQ, p, rows_max, s);
   return launch_back_t<MODE, float, float>(MQ, p, rows_max, s);
@@ -920,6 +942,22 @@ int kcs_version(void) { return 3; }
 
 int kcs_create_geometry(kcs_geometry_t** out, int nx, int ny, int nz, float vox_mm, int n_bins,
                         int n_angles, float bin_mm, int n_subsets) {
+  const int st = kcs_create_geometry_ex(out, nx, ny, nz, vox_mm, n_bins, n_angles, bin_mm,
+                                        n_subsets, nullptr);
+  if (st == KCS_OK) {
+    const cudaError_t e = cudaStreamSynchronize(nullptr);
+    if (e != cudaSuccess) {
+      kcs_destroy_geometry(*out);
+      *out = nullptr;
+      set_error("geometry tables: %s", cudaGetErrorString(e));
+      return KCS_ERR_CUDA;
+    }
+  }
+  return st;
+}
+
+int kcs_create_geometry_ex(kcs_geometry_t** out, int nx, int ny, int nz, float vox_mm,
+                           int n_bins, int n_angles, float bin_mm, int n_subsets, void* stream) {
   clear_error();
   KCS_REQUIRE(out != nullptr, "out is NULL");
   KCS_REQUIRE(nx > 0 && ny > 0 && nz > 0 && n_bins > 0 && n_angles > 0,
@@ -988,13 +1026,17 @@ int kcs_create_geometry(kcs_geometry_t** out, int nx, int ny, int nz, float vox_
   for (int a = 0; a < n_angles; ++a) g->h_angles.push_back(a);
   g->d_ang = nullptr;
   g->d_angles = nullptr;
+  // the host tables live in the geometry, so the copies may stay asynchronous
+  g->h_tab = tab;
+  cudaStream_t s = as_stream(stream);
   cudaError_t e = cudaMalloc(&g->d_ang, sizeof(AngleTab) * n_angles);
   if (e == cudaSuccess) e = cudaMalloc(&g->d_angles, sizeof(int) * g->h_angles.size());
   if (e == cudaSuccess)
-    e = cudaMemcpy(g->d_ang, tab.data(), sizeof(AngleTab) * n_angles, cudaMemcpyHostToDevice);
+    e = cudaMemcpyAsync(g->d_ang, g->h_tab.data(), sizeof(AngleTab) * n_angles,
+                        cudaMemcpyHostToDevice, s);
   if (e == cudaSuccess)
-    e = cudaMemcpy(g->d_angles, g->h_angles.data(), sizeof(int) * g->h_angles.size(),
-                   cudaMemcpyHostToDevice);
+    e = cudaMemcpyAsync(g->d_angles, g->h_angles.data(), sizeof(int) * g->h_angles.size(),
+                        cudaMemcpyHostToDevice, s);
   if (e != cudaSuccess) {
     set_error("geometry tables: %s", cudaGetErrorString(e));
     cudaFree(g->d_ang);
@@ -1043,6 +1085,45 @@ int kcs_forward_project(const kcs_geometry_t* g, int subset, int n_frames, const
   return KCS_OK;
 }
 
+int kcs_forward_project_ex(const kcs_geometry_t* g, int subset, int n_frames, const void* x,
+                           int x_type, const float* x_scale, float* y, void* stream) {
+  clear_error();
+  int st = check_geom(g, subset, n_frames);
+  if (st) return st;
+  KCS_REQUIRE(x_type == KCS_F32 || x_type == KCS_BF16 || x_type == KCS_F16,
+              "x_type %d must be KCS_F32, KCS_BF16 or KCS_F16", x_type);
+  KCS_REQUIRE(x && y, "x and y must be device pointers");
+  KCS_REQUIRE(aligned_for(x, x_type) && aligned16(y) && aligned16(x_scale),
+              "x must be 16-byte (float) or 8-byte (16-bit) aligned; y and x_scale 16-byte");
+  ProjArgs p = base_args(g, subset);
+  p.x = x;
+  p.xscale = reinterpret_cast<const float4*>(x_scale);
+  p.yout = y;
+  launch_forward_x(n_frames / 4, x_type, p, as_stream(stream));
+  KCS_LAUNCHED();
+  return KCS_OK;
+}
+
+int kcs_back_project_ex(const kcs_geometry_t* g, int subset, int n_frames, const void* y,
+                        int y_type, const float* y_scale, float* x, void* stream) {
+  clear_error();
+  int st = check_geom(g, subset, n_frames);
+  if (st) return st;
+  KCS_REQUIRE(y_type == KCS_F32 || y_type == KCS_BF16 || y_type == KCS_F16,
+              "y_type %d must be KCS_F32, KCS_BF16 or KCS_F16", y_type);
+  KCS_REQUIRE(x && y, "x and y must be device pointers");
+  KCS_REQUIRE(aligned_for(y, y_type) && aligned16(x) && aligned16(y_scale),
+              "y must be 16-byte (float) or 8-byte (16-bit) aligned; x and y_scale 16-byte");
+  ProjArgs p = base_args(g, subset);
+  p.y = y;
+  p.yscale = reinterpret_cast<const float4*>(y_scale);
+  p.xout = x;
+  st = launch_back<0>(n_frames / 4, y_type, p, back_rows_max(g), as_stream(stream));
+  if (st) return st;
+  KCS_LAUNCHED();
+  return KCS_OK;
+}
+
 int kcs_back_project(const kcs_geometry_t* g, int subset, int n_frames, const float* y, float* x,
                      void* stream) {
   clear_error();
@@ -1084,9 +1165,6 @@ size_t kcs_osl_workspace_size(const kcs_geometry_t* g, int n_frames) {
 }
 
 static bool storage_ok(int t) { return t == KCS_F32 || t == KCS_BF16 || t == KCS_F16; }
-static bool aligned_for(const void* ptr, int t) {
-  return ((uintptr_t)ptr & (t == KCS_F32 ? 15u : 7u)) == 0;
-}
 
 static int osl_ratio(const kcs_geometry_t* g, int subset, int n_frames, const float* frame_dt,
                      float kappa, const void* counts, int counts_type, const float* randoms,

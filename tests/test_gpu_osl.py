@@ -22,9 +22,9 @@ def _f32(a):
     return None if a is None else np.asarray(a, np.float32).astype(np.float64)
 
 
-def _small(seed=0, randoms="full", nf=True):
+def _small(seed=0, randoms="full", nf=True, bin_mm=2.0):
     nx, ny, nz, B, A, Sb, M = 37, 31, 2, 47, 36, 4, 8
-    og = OP.Geometry(nx, ny, 2.0, B, A, 2.0, Sb)
+    og = OP.Geometry(nx, ny, 2.0, B, A, bin_mm, Sb)
     rng = np.random.default_rng(seed)
     x_true = rng.uniform(0.5, 3.0, (nz, ny, nx, M))
     dt = np.linspace(0.25, 3.0, M)
@@ -57,6 +57,22 @@ def test_osl_update_matches_oracle(cuda_ok, randoms, prior):
         ref = OO.osl_update(og, x0, k, counts[:, og.subsets[k]], kappa, dt, n[:, og.subsets[k]],
                             None if rfull is None else rfull[:, og.subsets[k]],
                             F if prior else None, prior, 1.0)
+        assert rel_l2(xg.cpu().numpy(), ref) < 1e-4
+
+
+@pytest.mark.parametrize("bin_mm", [1.7, 2.6])
+def test_osl_update_other_bin_pitch(cuda_ok, bin_mm):
+    """Bins finer than the voxels (|beta| < 1 at some angles: up to three rays
+    reach a voxel per angle, the back-projection's general candidate loop) and
+    coarser ones (the two-candidate instance)."""
+    import paper_1803_10045_b300 as K
+    og, (nx, ny, nz, B, A, Sb, M), x0, dt, kappa, counts, r, n, F = _small(bin_mm=bin_mm)
+    kg = K.Geometry(nx, ny, nz, 2.0, B, A, bin_mm, Sb)
+    for k in range(Sb):
+        xg = _t(x0)
+        K.osl_update(kg, k, xg, _t(dt), kappa, _t(counts), _t(r), _t(n), _t(F), 2.0, 1.0)
+        ref = OO.osl_update(og, x0, k, counts[:, og.subsets[k]], kappa, dt, n[:, og.subsets[k]],
+                            r[:, og.subsets[k]], F, 2.0, 1.0)
         assert rel_l2(xg.cpu().numpy(), ref) < 1e-4
 
 

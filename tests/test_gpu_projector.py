@@ -127,3 +127,82 @@ def test_full_size_sampled_rays(cuda_ok):
         ref = P @ x[z].reshape(-1, M).double().cpu().numpy()
         got = y[z, ia].double().cpu().numpy()
         assert rel_l2(got, ref) < 2e-5
+
+
+KINDS = {"bf16": torch.bfloat16, "f16": torch.float16}
+
+
+@pytest.mark.parametrize("kind", ["bf16", "f16"])
+@pytest.mark.parametrize("case", [CASES[0], CASES[1], CASES[3]])
+def test_stored_forward_and_back_match_oracle(cuda_ok, case, kind):
+    """Precision form of the standalone projector: an image stored as
+    bfloat16 / float16 with a per-frame scale is projected (float32
+    accumulation) to the oracle's projection of the same stored values times
+    the scale; a stored sinogram is back-projected likewise.  The oracle sees
+    exactly the stored values (oracle.osl.quantize of the same numbers)."""
+    import paper_1803_10045_b300 as K
+    from oracle import osl as OO
+    kg, og = _pair(case)
+    nx, ny, nz, B, A, Sb, M, _ = case
+    rng = np.random.default_rng(5)
+    scale = rng.uniform(0.5, 4.0, M)
+    x = S.random_images((nz, ny, nx, M), seed=12)
+    xs = OO.quantize(x / scale, kind)                    # stored image values
+    xt = torch.tensor(xs, dtype=torch.float64).to(KINDS[kind]).cuda()
+    assert np.array_equal(xt.double().cpu().numpy(), xs)
+    sc = torch.tensor(scale, dtype=torch.float32, device="cuda")
+    sc64 = sc.double().cpu().numpy()
+    for k in [-1, 1]:
+        y = K.forward_project(kg, xt, k, x_scale=sc).double().cpu().numpy()
+        ref = og.forward(xs * sc64, None if k < 0 else k)
+        assert rel_l2(y, ref) < 2e-5, k
+        ys = OO.quantize(og.forward(x, None if k < 0 else k) / scale, kind)   # stored sinogram
+        yt = torch.tensor(ys, dtype=torch.float64).to(KINDS[kind]).cuda()
+        xb = K.back_project(kg, yt, k, y_scale=sc).double().cpu().numpy()
+        refb = og.back(ys * sc64, None if k < 0 else k)
+        assert rel_l2(xb, refb) < 2e-5, k
+
+
+def test_stored_calls_with_float32_equal_plain_calls(cuda_ok):
+    import paper_1803_10045_b300 as K
+    from paper_1803_10045_b300._lib import lib
+    import ctypes as C
+    kg, _ = _pair(CASES[1])
+    nx, ny, nz, B, A, Sb, M, _ = CASES[1]
+    x = torch.tensor(S.random_images((nz, ny, nx, M), seed=13), dtype=torch.float32,
+                     device="cuda")
+    y0 = K.forward_project(kg, x, 2)
+    y1 = torch.empty_like(y0)
+    st = C.c_void_p(torch.cuda.current_stream().cuda_stream)
+    assert lib.kcs_forward_project_ex(kg.handle, 2, M, C.c_void_p(x.data_ptr()), 0, None,
+                                      C.c_void_p(y1.data_ptr()), st) == 0
+    b0 = K.back_project(kg, y0, 2)
+    b1 = torch.empty_like(b0)
+    assert lib.kcs_back_project_ex(kg.handle, 2, M, C.c_void_p(y0.data_ptr()), 0, None,
+                                   C.c_void_p(b1.data_ptr()), st) == 0
+    torch.cuda.synchronize()
+    assert torch.equal(y0, y1) and torch.equal(b0, b1)
+
+
+def test_geometry_created_on_a_stream_equals_synchronous_one(cuda_ok):
+    """kcs_create_geometry_ex uploads the angle table on a stream; work issued
+    after it on that stream projects exactly as with the synchronous call."""
+    import ctypes as C
+    import paper_1803_10045_b300 as K
+    from paper_1803_10045_b300._lib import check, lib
+    nx, ny, nz, B, A, Sb, M, db = CASES[0]
+    kg = K.Geometry(nx, ny, nz, 2.0, B, A, db, Sb)
+    x = torch.tensor(S.random_images((nz, ny, nx, M), seed=14), dtype=torch.float32,
+                     device="cuda")
+    ref = K.forward_project(kg, x, -1)
+    s = torch.cuda.Stream()
+    with torch.cuda.stream(s):
+        h = C.c_void_p()
+        check(lib.kcs_create_geometry_ex(C.byref(h), nx, ny, nz, 2.0, B, A, db, Sb,
+                                         C.c_void_p(s.cuda_stream)))
+        y = torch.empty_like(ref)
+        check(lib.kcs_forward_project(h, -1, M, C.c_void_p(x.data_ptr()),
+                                      C.c_void_p(y.data_ptr()), C.c_void_p(s.cuda_stream)))
+    s.synchronize()
+    assert torch.equal(y, ref)
+    assert lib.kcs_destroy_geometry(h) == 0

@@ -321,3 +321,7 @@ def test_strict_voxels_rules():
     ref4 = ref.copy()
     ref4[1:3, v] = 0.0
     assert not lm.strict_voxels(sp, ref4, floor)[v]
+    # a larger allowance for the model error can only shrink the set
+    loose = lm.strict_voxels(sp, ref, floor, model_eps=0.0)
+    tight = lm.strict_voxels(sp, ref, floor, model_eps=1e-2)
+    assert np.all(loose | ~st) and np.all(st | ~tight) and tight.sum() < loose.sum()
