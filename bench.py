@@ -76,9 +76,10 @@ LM_FLOPS_PER_VOXEL_STEP = lm_flops_per_voxel_step(frames=S.WORKLOADS["pr2"].n_fr
 # planes: every kernel touches each plane's data independently), valid while
 # the kernel's source file is unchanged (sha256 prefix); see profiles/.
 TRAFFIC = {
-    "lm_step": {"bytes": 470.39e6 * 127 / 16, "src": "kinetics.cu", "sha": "46b7a807e9961c7f"},
-    "bwd_osl": {"bytes": 509.05e6 * 127 / 16, "src": "projector.cu", "sha": "9cb7fafdca0e9c59"},
-    "fwd_ratio": {"bytes": 266.50e6 * 127 / 16, "src": "projector.cu", "sha": "9cb7fafdca0e9c59"},
+    "lm_step": {"bytes": 472.13e6 * 127 / 16, "src": "kinetics.cu", "sha": "4bac6bfff89490ca"},
+    "bwd_osl": {"bytes": 510.75e6 * 127 / 16, "src": "projector.cu", "sha": "dc55fab8849596de"},
+    "fwd_ratio": {"bytes": 258.43e6 * 127 / 16, "src": "projector.cu", "sha": "dc55fab8849596de"},
+    "tac_eval": {"bytes": 153.38e6 * 127 / 16, "src": "kinetics.cu", "sha": "4bac6bfff89490ca"},
 }
 
 
