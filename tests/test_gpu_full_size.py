@@ -112,7 +112,8 @@ def test_full_size_lm_step_sampled_voxels(cuda_ok):
     # the centre voxel of window k is voxel 9 k + 4 of the flattened result
     sp = OL.float32_spread(win_x, win_maps, win_lam, ts, te, S.FENG, beta, delta)
     ctr = np.arange(n) * 9 + 4
-    keys = ("acc", "trial", "xi", "flip", "margin", "dev_trial", "dev_margin")
+    keys = ("acc", "trial", "xi", "flip", "margin", "dev_trial", "dev_margin", "model_margin",
+            "huber_margin")
     spc = {k: sp[k][ctr] for k in keys}
     # lambda spans 1e-6 .. 10 here, so more steps are float32-sensitive than on
     # PR1 (the share is fixed by the oracle: 73 % strict on these inputs)
