@@ -209,6 +209,14 @@ __global__ void k_frame_tables(const double* m0, const int* code, int n_iv, cons
   fr_cp[m] = (float)(s / fdt[m]);
 }
 
+// One table entry (the A and B cubics of a cell and frame, 32 bytes, 32-byte
+// aligned) by a single 256-bit read-only load.
+__device__ __forceinline__ void ld_cell(const float4* p, float4& a, float4& b) {
+  asm("ld.global.nc.v8.f32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
+      : "=f"(a.x), "=f"(a.y), "=f"(a.z), "=f"(a.w), "=f"(b.x), "=f"(b.y), "=f"(b.z), "=f"(b.w)
+      : "l"(p));
+}
+
 // ---------------------------------------------------------------- model
 // Evaluates F_m (and dF_m/d(K1,k2,k3,Vb) when JAC) of VPT voxels frame by frame
 // and hands each frame to sink(v, m, F, J0, J1, J2, J3).  With w = 1 - Vb and
@@ -239,8 +247,8 @@ __device__ __forceinline__ void eval_model(const KinDev& kd, const float (&K1)[V
     const float4* row = kd.cell + (size_t)m * N_CELLS * 2;
 #pragma unroll
     for (int v = 0; v < VPT; ++v) {
-      const float4 ca = __ldg(row + 2 * j[v]);
-      const float4 cb = __ldg(row + 2 * j[v] + 1);
+      float4 ca, cb;
+      ld_cell(row + 2 * j[v], ca, cb);
       const float A = fmaf(t[v], fmaf(t[v], fmaf(t[v], ca.w, ca.z), ca.y), ca.x);
       const float B = fmaf(t[v], fmaf(t[v], fmaf(t[v], cb.w, cb.z), cb.y), cb.x);
       const float S = fmaf(k3[v], B, A);

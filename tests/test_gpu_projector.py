@@ -206,3 +206,27 @@ def test_geometry_created_on_a_stream_equals_synchronous_one(cuda_ok):
     s.synchronize()
     assert torch.equal(y, ref)
     assert lib.kcs_destroy_geometry(h) == 0
+
+
+def test_forward_of_an_image_aligned_to_16_bytes_only(cuda_ok):
+    """The ABI promises 16-byte alignment only: an image placed 16 bytes off a
+    32-byte boundary projects to the same bits as an aligned copy, plain and
+    fused with the ratio."""
+    import paper_1803_10045_b300 as K
+    nx, ny, nz, B, A, Sb, M, db = (33, 29, 2, 40, 36, 4, 24, 2.0)
+    kg = K.Geometry(nx, ny, nz, 2.0, B, A, db, Sb)
+    x = torch.tensor(S.random_images((nz, ny, nx, M), seed=15), dtype=torch.float32,
+                     device="cuda")
+    buf = torch.empty(x.numel() + 8, dtype=torch.float32, device="cuda")
+    off = 4 if buf.data_ptr() % 32 == 0 else 0      # floats: 16 bytes off a 32-byte boundary
+    xs = buf[off:off + x.numel()].view(x.shape)
+    xs.copy_(x)
+    assert xs.data_ptr() % 16 == 0 and xs.data_ptr() % 32 != 0
+    assert x.data_ptr() % 32 == 0
+    for k in (-1, 1):
+        assert torch.equal(K.forward_project(kg, x, k), K.forward_project(kg, xs, k))
+    dt = torch.linspace(0.5, 3.0, M, device="cuda")
+    counts = torch.poisson(K.forward_project(kg, x, -1) * dt * 3.0)
+    r1 = K.osl_ratio(kg, 2, x, dt, 3.0, counts)
+    r2 = K.osl_ratio(kg, 2, xs, dt, 3.0, counts)
+    assert torch.equal(r1[..., :M], r2[..., :M])     # the row pitch pads frames M.. unwritten
