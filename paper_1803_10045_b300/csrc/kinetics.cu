@@ -25,6 +25,7 @@
 
 #include <cmath>
 #include <algorithm>
+#include <type_traits>
 #include <mutex>
 
 #include "kcs_internal.cuh"
@@ -457,8 +458,9 @@ struct LmArgs {
   float beta, delta;
   float tau;             // accept iff the objective falls by more than tau of its value
   int nb3d;              // Huber neighbourhood: 0 in-plane 3x3, 1 the 3x3x3 cube
-  const float* ne_in;    // [16][V] normal equations at the current point
-  float* ne_out;         // [16][V] normal equations at the returned point
+  int x_al32;            // x starts on a 32-byte boundary
+  const float* ne_in;    // [V][16] normal equations at the current point
+  float* ne_out;         // [V][16] normal equations at the returned point
   unsigned long long div_nx, div_nxy;   // div_magic64(nx), div_magic64(nx ny)
 };
 
@@ -618,8 +620,9 @@ __device__ __forceinline__ void huber_terms(const LmArgs& L, long long V, long l
 }
 
 // The damped normal equations of a voxel at its current point, kept between
-// steps in the workspace as 16 floats [16][V]: A00 A01 A02 A03 A11 A12 A13 A22
-// A23 A33, b0..b3 (J^T r), and the compensated sum of squared residuals (s, c).
+// steps in the workspace as 16 contiguous floats per voxel, [V][16] (64 bytes,
+// moved by two 256-bit accesses): A00 A01 A02 A03 A11 A12 A13 A22 A23 A33,
+// b0..b3 (J^T r), and the compensated sum of squared residuals (s, c).
 constexpr int NE_FIELDS = 16;
 
 __device__ __forceinline__ void store_normal(float* ne, long long V, long long v, const Normal& n,
@@ -627,14 +630,26 @@ __device__ __forceinline__ void store_normal(float* ne, long long V, long long v
   const float f[NE_FIELDS] = {n.A00, n.A01, n.A02, n.A03, n.A11, n.A12, n.A13, n.A22,
                               n.A23, n.A33, n.b0,  n.b1,  n.b2,  n.b3,  rr.s,  rr.c};
 #pragma unroll
-  for (int q = 0; q < NE_FIELDS; ++q) ne[q * V + v] = f[q];
+  float* o = ne + (size_t)v * NE_FIELDS;
+  asm volatile("st.global.v8.f32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8};" ::"l"(o), "f"(f[0]),
+               "f"(f[1]), "f"(f[2]), "f"(f[3]), "f"(f[4]), "f"(f[5]), "f"(f[6]), "f"(f[7]) : "memory");
+  asm volatile("st.global.v8.f32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8};" ::"l"(o + 8), "f"(f[8]),
+               "f"(f[9]), "f"(f[10]), "f"(f[11]), "f"(f[12]), "f"(f[13]), "f"(f[14]), "f"(f[15])
+               : "memory");
 }
 
 __device__ __forceinline__ void load_normal(const float* ne, long long V, long long v, Normal& n,
                                             KSum& rr) {
   float f[NE_FIELDS];
 #pragma unroll
-  for (int q = 0; q < NE_FIELDS; ++q) f[q] = __ldg(ne + q * V + v);
+  const float* o = ne + (size_t)v * NE_FIELDS;
+  asm("ld.global.nc.v8.f32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
+      : "=f"(f[0]), "=f"(f[1]), "=f"(f[2]), "=f"(f[3]), "=f"(f[4]), "=f"(f[5]), "=f"(f[6]), "=f"(f[7])
+      : "l"(o));
+  asm("ld.global.nc.v8.f32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
+      : "=f"(f[8]), "=f"(f[9]), "=f"(f[10]), "=f"(f[11]), "=f"(f[12]), "=f"(f[13]), "=f"(f[14]),
+        "=f"(f[15])
+      : "l"(o + 8));
   n = Normal{f[0], f[1], f[2], f[3], f[4], f[5], f[6], f[7], f[8], f[9], f[10], f[11], f[12], f[13]};
   rr = KSum{f[14], f[15]};
 }
@@ -646,6 +661,25 @@ __device__ __forceinline__ void stage_tacs(const LmArgs& L, float* xs_all, long 
   const int M = L.kd.M;
   const int ld = M + 1;
   const TX* xg = static_cast<const TX*>(L.x) + v0 * M;
+  if constexpr (std::is_same<TX, float>::value) {
+    if (L.x_al32 && (M & 7) == 0) {
+      // 8 frames of one voxel per 256-bit load (M is a multiple of 8)
+      for (int e8 = threadIdx.x; e8 < (int)nv * M / 8; e8 += LM_THREADS) {
+        const int e = 8 * e8;
+        const int r = (int)__umulhi((unsigned)e, L.kd.div_m), m = e - r * M;
+        float v[8];
+        asm("ld.global.nc.v8.f32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
+            : "=f"(v[0]), "=f"(v[1]), "=f"(v[2]), "=f"(v[3]), "=f"(v[4]), "=f"(v[5]), "=f"(v[6]),
+              "=f"(v[7])
+            : "l"(xg + e));
+#pragma unroll
+        for (int u = 0; u < 8; ++u)
+          xs_all[r * ld + m + u] = L.x_scale ? v[u] * __ldg(L.x_scale + m + u) : v[u];
+      }
+      __syncthreads();
+      return;
+    }
+  }
   // e < LM_BLOCK_VOX * 32: the multiply-high quotient is exact
   for (int e = threadIdx.x; e < (int)nv * M; e += LM_THREADS) {
     const int r = (int)__umulhi((unsigned)e, L.kd.div_m), m = e - r * M;
@@ -765,7 +799,10 @@ __global__ void __launch_bounds__(LM_THREADS, KCS_LM_MINBLOCKS) k_lm_step(LmArgs
       store_normal(L.ne_out, V, v, ns.n[k], ns.rr[k]);
     } else {
 #pragma unroll
-      for (int q = 0; q < NE_FIELDS; ++q) L.ne_out[q * V + v] = __ldg(L.ne_in + q * V + v);
+      Normal nk;
+      KSum rk;
+      load_normal(L.ne_in, V, v, nk, rk);
+      store_normal(L.ne_out, V, v, nk, rk);
     }
   }
 }
@@ -1009,6 +1046,7 @@ int kcs_map_lm_fit_nb(const kcs_kinetics_t* k, int nx, int ny, int nz, const voi
   L.kd = k->dev();
   L.nx = nx; L.ny = ny; L.nz = nz;
   L.x = x;
+  L.x_al32 = ((uintptr_t)x & 31u) == 0;
   L.x_scale = x_scale;
   L.lambda = lambda ? lambda : lam_ws;
   L.beta = beta_h;

@@ -230,3 +230,10 @@ def test_forward_of_an_image_aligned_to_16_bytes_only(cuda_ok):
     r1 = K.osl_ratio(kg, 2, x, dt, 3.0, counts)
     r2 = K.osl_ratio(kg, 2, xs, dt, 3.0, counts)
     assert torch.equal(r1[..., :M], r2[..., :M])     # the row pitch pads frames M.. unwritten
+    # the OSL update reads and writes the image by 256-bit accesses only when
+    # it and the model TACs are 32-byte aligned; the 16-byte path gives the same bits
+    F = x * 0.9
+    xa, xb = x.clone(), xs
+    K.osl_update(kg, 2, xa, dt, 3.0, counts, F=F, beta=0.5)
+    K.osl_update(kg, 2, xb, dt, 3.0, counts, F=F, beta=0.5)
+    assert torch.equal(xa, xb)
