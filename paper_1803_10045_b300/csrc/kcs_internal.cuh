@@ -72,7 +72,8 @@ struct __align__(16) AngleTab {
   float centre;    // (n_minor - 1) / 2: centre of the minor axis
   float rband;     // |1 / beta| + 1e-3: half-width in bins of the candidates of a voxel
   int pair;        // 1: at most two consecutive bins reach any voxel (see kcs_create_geometry)
-  int pad_[3];
+  int pad_[3];     // spare; the back-projection's staged copy carries a block's row
+                   // window (first row, row count) and the angle index here
 };
 
 }  // namespace kcs

@@ -593,6 +593,11 @@ __global__ void __launch_bounds__(BK_TILE * BK_TILE, 4) k_back_bulk(ProjArgs p, 
         hi = min(p.B - 1, hi + 1);
         s_lo[threadIdx.x] = lo;
         s_cnt[threadIdx.x] = max(0, min(hi - lo + 1, rows_max));
+        // the same three integers in the entry's spare words: one 48-byte
+        // entry per angle is all the pair path reads
+        s_T[threadIdx.x].pad_[0] = lo;
+        s_T[threadIdx.x].pad_[1] = max(0, min(hi - lo + 1, rows_max));
+        s_T[threadIdx.x].pad_[2] = a;
       }
       __syncwarp();
       if (threadIdx.x == 0) {
@@ -613,15 +618,15 @@ __global__ void __launch_bounds__(BK_TILE * BK_TILE, 4) k_back_bulk(ProjArgs p, 
     for (int c = 0; c < na; ++c) {
       ok = mbar_wait(&s_bar[c], parity) && ok;
       if (!valid || !ok) continue;
-      const int a = s_a[c];
       const AngleTab T = s_T[c];
+      const int a = (MODE == 1 && PAIR) ? T.pad_[2] : s_a[c];
       const int t = T.xmajor ? i : j;
       const int m = T.xmajor ? j : i;
       const float inner = inner_pos((float)t - T.tc, T.gamma, T.centre);
       // candidates: bins within |1/beta| (+1e-3) of the real bin u whose ray
       // meets minor index m; the exact test below decides
       const float u = fmaf((float)m - inner, T.inv_beta, bc);
-      const int lo = s_lo[c];
+      const int lo = (MODE == 1 && PAIR) ? T.pad_[0] : s_lo[c];
       const TY* rows = reinterpret_cast<const TY*>(sraw + (size_t)c * rows_max * RB);
       const size_t binrow = (size_t)(z * p.A + a) * p.B;
       if (MODE == 1 && PAIR) {
@@ -632,7 +637,7 @@ __global__ void __launch_bounds__(BK_TILE * BK_TILE, 4) k_back_bulk(ProjArgs p, 
         // candidates are then processed without a loop or a branch, in
         // ascending bin order as the forward's triples are summed (a zero
         // weight adds exactly nothing: the staged ratios are finite).
-        const int cnt = s_cnt[c];
+        const int cnt = T.pad_[1];
         if (cnt == 0) continue;                            // no staged row reaches the tile
         const float mf = (float)m;
         const float kf = rintf(u);
