@@ -118,3 +118,51 @@ def test_full_size_lm_step_sampled_voxels(cuda_ok):
     # lambda spans 1e-6 .. 10 here, so more steps are float32-sensitive than on
     # PR1 (the share is fixed by the oracle: 73 % strict on these inputs)
     lm_step_parity(got.T, lam_g, win_lam[:, 1, 1], spc, 0.6, "PR2 sampled voxels")
+
+
+def test_full_size_plane_shards_equal_full_volume(cuda_ok):
+    """Plane sharding of the product path at full size: the CUDA ICM run on
+    each rank's contiguous plane range (plane_shard, 4 ranks, emulated one
+    after another on this GPU) equals the full 127-plane run restricted to
+    those planes bit for bit, image, maps and model TACs.  No cross-plane
+    term exists in the projector, the OSL update, the in-plane Huber prior or
+    the LM step, so a multi-GPU run needs no data-path exchange.  The start
+    image is the full volume's (its per-frame level is a sum over all planes)."""
+    import paper_1803_10045_b300 as K
+    from paper_1803_10045_b300.sharding import plane_shard
+    W = S.WORKLOADS["pr2"]
+    ts, te = W.frames()
+    M = W.n_frames
+    g = K.Geometry(W.nx, W.ny, W.nz, W.vox_mm, W.n_bins, W.n_angles, W.bin_mm, W.n_subsets)
+    kin = K.Kinetics(ts, te, S.FENG)
+    dt = torch.tensor(te - ts, dtype=torch.float32, device="cuda")
+    xi = torch.tensor(S.phantom_pr2(W.nx, W.nz, seed=3), device="cuda")
+    ybar = K.forward_project(g, K.tac_eval(kin, xi)).mul_(dt)
+    kappa = _f32(W.total_prompts * (1 - W.randoms_frac) / ybar.double().sum().item())
+    r = (W.total_prompts * W.randoms_frac) * dt / (dt.sum() * W.nz * W.n_angles * W.n_bins)
+    counts = torch.poisson(ybar.mul_(kappa).add_(r),
+                           generator=torch.Generator(device="cuda").manual_seed(3))
+    del ybar, xi
+    counts = counts.to(torch.uint16)                       # the benchmark's counts type
+    x0 = K.init_image(g, dt, kappa, counts, r)
+    p0 = torch.empty((4, W.nz, W.ny, W.nx), device="cuda")
+    p0[:] = torch.tensor(S.XI0, device="cuda")[:, None, None, None]
+    kw = dict(randoms=r, n_lm=10, beta_kp=0.1, beta_h=0.1, delta=0.01)
+
+    def run(geom, c, x, p):
+        F = torch.zeros(x.shape, device="cuda")
+        K.Study(geom, kin, dt, kappa, c, x, p, F=F, **kw).iterate(2)
+        return F
+    x, p = x0.clone(), p0.clone()
+    F = run(g, counts, x, p)
+    world = 4
+    for rank in range(world):
+        z0, z1 = plane_shard(W.nz, rank, world)
+        gs = K.Geometry(W.nx, W.ny, z1 - z0, W.vox_mm, W.n_bins, W.n_angles, W.bin_mm,
+                        W.n_subsets)
+        xs, ps = x0[z0:z1].clone(), p0[:, z0:z1].contiguous()
+        Fs = run(gs, counts[z0:z1].contiguous(), xs, ps)
+        torch.cuda.synchronize()
+        assert torch.equal(xs, x[z0:z1]), f"rank {rank} image"
+        assert torch.equal(ps, p[:, z0:z1]), f"rank {rank} maps"
+        assert torch.equal(Fs, F[z0:z1]), f"rank {rank} model TACs"
