@@ -629,7 +629,6 @@ __device__ __forceinline__ void store_normal(float* ne, long long V, long long v
                                              const KSum& rr) {
   const float f[NE_FIELDS] = {n.A00, n.A01, n.A02, n.A03, n.A11, n.A12, n.A13, n.A22,
                               n.A23, n.A33, n.b0,  n.b1,  n.b2,  n.b3,  rr.s,  rr.c};
-#pragma unroll
   float* o = ne + (size_t)v * NE_FIELDS;
   asm volatile("st.global.v8.f32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8};" ::"l"(o), "f"(f[0]),
                "f"(f[1]), "f"(f[2]), "f"(f[3]), "f"(f[4]), "f"(f[5]), "f"(f[6]), "f"(f[7]) : "memory");
@@ -641,7 +640,6 @@ __device__ __forceinline__ void store_normal(float* ne, long long V, long long v
 __device__ __forceinline__ void load_normal(const float* ne, long long V, long long v, Normal& n,
                                             KSum& rr) {
   float f[NE_FIELDS];
-#pragma unroll
   const float* o = ne + (size_t)v * NE_FIELDS;
   asm("ld.global.nc.v8.f32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
       : "=f"(f[0]), "=f"(f[1]), "=f"(f[2]), "=f"(f[3]), "=f"(f[4]), "=f"(f[5]), "=f"(f[6]), "=f"(f[7])
@@ -798,7 +796,6 @@ __global__ void __launch_bounds__(LM_THREADS, KCS_LM_MINBLOCKS) k_lm_step(LmArgs
     if (accept) {
       store_normal(L.ne_out, V, v, ns.n[k], ns.rr[k]);
     } else {
-#pragma unroll
       Normal nk;
       KSum rk;
       load_normal(L.ne_in, V, v, nk, rk);
