@@ -76,10 +76,10 @@ LM_FLOPS_PER_VOXEL_STEP = lm_flops_per_voxel_step(frames=S.WORKLOADS["pr2"].n_fr
 # planes: every kernel touches each plane's data independently), valid while
 # the kernel's source file is unchanged (sha256 prefix); see profiles/.
 TRAFFIC = {
-    "lm_step": {"bytes": 473.08e6 * 127 / 16, "src": "kinetics.cu", "sha": "8ea722a731e0f4ea"},
+    "lm_step": {"bytes": 473.25e6 * 127 / 16, "src": "kinetics.cu", "sha": "35a59baed8d29173"},
     "bwd_osl": {"bytes": 515.09e6 * 127 / 16, "src": "projector.cu", "sha": "3efd6170d0b11f75"},
     "fwd_ratio": {"bytes": 264.26e6 * 127 / 16, "src": "projector.cu", "sha": "3efd6170d0b11f75"},
-    "tac_eval": {"bytes": 154.05e6 * 127 / 16, "src": "kinetics.cu", "sha": "8ea722a731e0f4ea"},
+    "tac_eval": {"bytes": 153.50e6 * 127 / 16, "src": "kinetics.cu", "sha": "35a59baed8d29173"},
 }
 
 
