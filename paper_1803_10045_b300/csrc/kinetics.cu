@@ -433,11 +433,11 @@ __global__ void k_huber_grad(int nx, int ny, int nz, const float* p, float delta
 #ifndef KCS_LM_CARVEOUT
 #define KCS_LM_CARVEOUT 50   // percent of the maximum shared memory per SM
 #endif
-// frames per trip of the model loop in the LM kernels (1 measured 1 % faster
-// than 2 at 64 registers; 4 gains nothing, 80 registers for 6 blocks per SM
-// lose 20 %)
+// frames per trip of the model loop in the LM kernels: 2 (64 registers),
+// 1 % faster than 1 now that the table reads are served from L2; 80
+// registers for 6 blocks per SM lose 20 %, 2 voxels per thread 80 %
 #ifndef KCS_LM_UNROLL
-#define KCS_LM_UNROLL 1
+#define KCS_LM_UNROLL 2
 #endif
 #ifndef KCS_LM_MINBLOCKS
 #define KCS_LM_MINBLOCKS 8
