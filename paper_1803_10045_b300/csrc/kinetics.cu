@@ -683,6 +683,33 @@ __device__ __forceinline__ void stage_tacs(const LmArgs& L, float* xs_all, long 
       return;
     }
   }
+  if constexpr (!std::is_same<TX, float>::value) {
+    if (L.x_al32 && (M & 7) == 0) {
+      // 8 frames of one voxel per 16-byte load (read once: no L1 allocation),
+      // converted exactly to float32
+      for (int e8 = threadIdx.x; e8 < (int)nv * M / 8; e8 += LM_THREADS) {
+        const int e = 8 * e8;
+        const int r = (int)__umulhi((unsigned)e, L.kd.div_m), m = e - r * M;
+        uint32_t w[4];
+        asm("ld.global.nc.L1::no_allocate.v4.u32 {%0, %1, %2, %3}, [%4];"
+            : "=r"(w[0]), "=r"(w[1]), "=r"(w[2]), "=r"(w[3])
+            : "l"(xg + e));
+#pragma unroll
+        for (int h = 0; h < 4; ++h) {
+          float2 f;
+          if constexpr (std::is_same<TX, __nv_bfloat16>::value)
+            f = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&w[h]));
+          else
+            f = __half22float2(*reinterpret_cast<const __half2*>(&w[h]));
+          const int mm = m + 2 * h;
+          xs_all[r * ld + mm] = L.x_scale ? f.x * __ldg(L.x_scale + mm) : f.x;
+          xs_all[r * ld + mm + 1] = L.x_scale ? f.y * __ldg(L.x_scale + mm + 1) : f.y;
+        }
+      }
+      __syncthreads();
+      return;
+    }
+  }
   // e < LM_BLOCK_VOX * 32: the multiply-high quotient is exact
   for (int e = threadIdx.x; e < (int)nv * M; e += LM_THREADS) {
     const int r = (int)__umulhi((unsigned)e, L.kd.div_m), m = e - r * M;
