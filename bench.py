@@ -76,11 +76,38 @@ LM_FLOPS_PER_VOXEL_STEP = lm_flops_per_voxel_step(frames=S.WORKLOADS["pr2"].n_fr
 # planes: every kernel touches each plane's data independently), valid while
 # the kernel's source file is unchanged (sha256 prefix); see profiles/.
 TRAFFIC = {
-    "lm_step": {"bytes": 473.25e6 * 127 / 16, "src": "kinetics.cu", "sha": "35a59baed8d29173"},
+    "lm_step": {"bytes": 473.62e6 * 127 / 16, "src": "kinetics.cu", "sha": "55a292b0e0d79625"},
     "bwd_osl": {"bytes": 515.09e6 * 127 / 16, "src": "projector.cu", "sha": "3efd6170d0b11f75"},
     "fwd_ratio": {"bytes": 264.26e6 * 127 / 16, "src": "projector.cu", "sha": "3efd6170d0b11f75"},
-    "tac_eval": {"bytes": 153.50e6 * 127 / 16, "src": "kinetics.cu", "sha": "35a59baed8d29173"},
+    "tac_eval": {"bytes": 153.51e6 * 127 / 16, "src": "kinetics.cu", "sha": "55a292b0e0d79625"},
 }
+
+
+def joseph_nnz_per_subset(W):
+    """Mean number of nonzero Joseph-matrix entries (voxel, bin) of one plane
+    and one subset: every in-grid interpolation partner with a positive weight
+    of every ray sample (the positions the projector kernels compute, here in
+    float64).  Each
+    entry moves one M-frame vector through the SM data path: an image vector
+    in the forward projection, a ratio vector in the back-projection."""
+    B, A = W.n_bins, W.n_angles
+    bf = np.arange(B) - 0.5 * (B - 1)
+    total = 0
+    for a in range(A):
+        c, s = np.cos(a * np.pi / A), np.sin(a * np.pi / A)
+        if A <= 4 * a <= 3 * A:                            # steps over x
+            beta, gamma, n_major, n_minor = W.bin_mm / (s * W.vox_mm), -c / s, W.nx, W.ny
+        else:
+            beta, gamma, n_major, n_minor = W.bin_mm / (c * W.vox_mm), -s / c, W.ny, W.nx
+        tf = np.arange(n_major) - 0.5 * (n_major - 1)
+        fr = bf[:, None] * beta + (tf[None, :] * gamma + 0.5 * (n_minor - 1))
+        j0 = np.floor(fr)
+        total += np.count_nonzero((j0 >= 0) & (j0 < n_minor))                    # weight 1 - f > 0
+        total += np.count_nonzero((j0 >= -1) & (j0 < n_minor - 1) & (fr > j0))   # weight f > 0
+    return total / W.n_subsets
+
+
+L1_BYTES_PER_CYCLE = 128   # L1 / shared-memory data path of one SM
 
 
 def _traffic(kernel):
@@ -441,6 +468,17 @@ def run_ours(args):
                          "alg_GBps": round(alg[name] / (avg * 1e-3) / 1e9, 1),
                          "frac_hbm": round(alg[name] / (avg * 1e-3) / 1e9 / hbm, 4),
                          "traffic_GB": _traffic(name) if args.storage == "f32" else None}
+    # the projectors' own limit: the frame vectors of the Joseph matrix's
+    # nonzeros through the L1 / shared-memory data path, against its byte rate
+    # at the SM clock measured during the timed region
+    sm_mhz = clocks.get("sm_mhz") or smax
+    l1_peak = N_SM * L1_BYTES_PER_CYCLE * sm_mhz * 1e6 / 1e12
+    nnz = joseph_nnz_per_subset(W) * W.nz
+    for name in ("fwd_ratio", "bwd_osl"):
+        l1_b = nnz * M * es
+        l1_tb = l1_b / (kernels[name]["avg_ms"] * 1e-3) / 1e12
+        kernels[name].update({"l1_GB": round(l1_b / 1e9, 2), "l1_TBps": round(l1_tb, 2),
+                              "l1_peak_TBps": round(l1_peak, 1), "frac_l1": round(l1_tb / l1_peak, 4)})
     dom = max(kernels, key=lambda n: kernels[n]["share"])
     fp32_peak = fp32_meas["flops_per_s"] / 1e12
     fp32_src = (f"measured FFMA rate, kcs_fma_peak_launch ({fp32_meas['blocks']} blocks x 256 "

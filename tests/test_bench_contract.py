@@ -40,3 +40,21 @@ def test_gpu_arm_tables_well_formed():
         got = bench._traffic(name)
         # None only when the kernel source changed since the counters were taken
         assert got is None or got > 1.0, name
+
+
+def test_joseph_nonzero_count_matches_oracle_matrix():
+    """The bench's count of Joseph-matrix nonzeros (the frame vectors the
+    projectors move through the SM data path) equals the number of stored
+    entries of the oracle's system matrix, over all angles, for bins equal to
+    and finer than the voxels."""
+    from types import SimpleNamespace
+
+    import bench
+    from oracle import projector as OP
+    for n_bins, bin_mm, n_angles, n_subsets in ((40, 2.0, 36, 4), (48, 1.7, 30, 5)):
+        W = SimpleNamespace(nx=32, ny=28, vox_mm=2.0, n_bins=n_bins, bin_mm=bin_mm,
+                            n_angles=n_angles, n_subsets=n_subsets)
+        nnz = OP.system_matrix(W.nx, W.ny, W.vox_mm, n_bins, n_angles, bin_mm).nnz
+        got = bench.joseph_nnz_per_subset(W) * n_subsets
+        print(f"bins {n_bins} x {bin_mm} mm: bench {got:.0f}, oracle {nnz}")
+        assert abs(got - nnz) <= 1e-3 * nnz
