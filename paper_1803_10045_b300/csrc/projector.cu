@@ -453,11 +453,14 @@ __global__ void __launch_bounds__(BK_TILE * BK_TILE) k_back_tiled(ProjArgs p, in
       den.z = fmaxf(fmaf(ps, xv.z - Fv.z, den.z), 1e-3f * den.z);
       den.w = fmaxf(fmaf(ps, xv.w - Fv.w, den.w), 1e-3f * den.w);
     }
+    // a stored 16-bit image: activity -> stored value in the one division
+    if (!std::is_same<TX, float>::value && p.xscale) den = mul4(den, sc);
     xv.x = __fdividef(xv.x * (p.kappa * dt.x * acc[q].x), den.x);
     xv.y = __fdividef(xv.y * (p.kappa * dt.y * acc[q].y), den.y);
     xv.z = __fdividef(xv.z * (p.kappa * dt.z * acc[q].z), den.z);
     xv.w = __fdividef(xv.w * (p.kappa * dt.w * acc[q].w), den.w);
-    if (p.xscale) xv = make_float4(xv.x / sc.x, xv.y / sc.y, xv.z / sc.z, xv.w / sc.w);
+    if (std::is_same<TX, float>::value && p.xscale)
+      xv = make_float4(xv.x / sc.x, xv.y / sc.y, xv.z / sc.z, xv.w / sc.w);
     st4(static_cast<TX*>(p.xout) + (vi + q) * 4, xv);
   }
 }
@@ -704,7 +707,7 @@ __global__ void __launch_bounds__(BK_TILE * BK_TILE, 4) k_back_bulk(ProjArgs p, 
   if (!(sens > 0.f)) return;   // x unchanged where no ray of the subset sees the voxel
   const float ks = p.kappa * sens;
   if constexpr (std::is_same<TX, float>::value && MQ % 2 == 0) {
-    if (p.aligned32) {
+    if (p.aligned32 && !p.xscale) {
       // image and model frame vectors by 256-bit loads and stores (half the
       // requests of 16-byte ones)
 #pragma unroll
@@ -736,11 +739,14 @@ __global__ void __launch_bounds__(BK_TILE * BK_TILE, 4) k_back_bulk(ProjArgs p, 
       den.z = fmaxf(fmaf(ps, xv.z - Fv.z, den.z), 1e-3f * den.z);
       den.w = fmaxf(fmaf(ps, xv.w - Fv.w, den.w), 1e-3f * den.w);
     }
+    // a stored 16-bit image: activity -> stored value in the one division
+    if (!std::is_same<TX, float>::value && p.xscale) den = mul4(den, sc);
     xv.x = __fdividef(xv.x * (p.kappa * dt.x * acc[q].x), den.x);
     xv.y = __fdividef(xv.y * (p.kappa * dt.y * acc[q].y), den.y);
     xv.z = __fdividef(xv.z * (p.kappa * dt.z * acc[q].z), den.z);
     xv.w = __fdividef(xv.w * (p.kappa * dt.w * acc[q].w), den.w);
-    if (p.xscale) xv = make_float4(xv.x / sc.x, xv.y / sc.y, xv.z / sc.z, xv.w / sc.w);
+    if (std::is_same<TX, float>::value && p.xscale)
+      xv = make_float4(xv.x / sc.x, xv.y / sc.y, xv.z / sc.z, xv.w / sc.w);
     st4(static_cast<TX*>(p.xout) + (vi + q) * 4, xv);
   }
 }

@@ -60,6 +60,30 @@ def test_osl_update_matches_oracle(cuda_ok, randoms, prior):
         assert rel_l2(xg.cpu().numpy(), ref) < 1e-4
 
 
+@pytest.mark.parametrize("prior", [0.0, 2.0])
+def test_osl_update_float_storage_with_scale(cuda_ok, prior):
+    """Float32 storage with a per-frame scale (x held as x / scale[m]; the ABI
+    takes a scale for every storage type): the stored update times the scale
+    equals the oracle's update of the activity, on 32-byte-aligned arrays of
+    an even frame-quad count (where the unscaled update uses 256-bit
+    accesses)."""
+    import paper_1803_10045_b300 as K
+    og, (nx, ny, nz, B, A, Sb, M), x0, dt, kappa, counts, r, n, F = _small()
+    kg = K.Geometry(nx, ny, nz, 2.0, B, A, 2.0, Sb)
+    assert (M // 4) % 2 == 0
+    scale = _f32(np.linspace(0.5, 4.0, M))
+    stored = _f32(x0 / scale)
+    for k in range(Sb):
+        xs = _t(stored)
+        assert xs.data_ptr() % 32 == 0
+        K.osl_update(kg, k, xs, _t(dt), kappa, _t(counts), _t(r), _t(n),
+                     _t(F) if prior else None, prior, 1.0, x_scale=_t(scale))
+        ref = OO.osl_update(og, stored * scale, k, counts[:, og.subsets[k]], kappa, dt,
+                            n[:, og.subsets[k]], r[:, og.subsets[k]], F if prior else None,
+                            prior, 1.0)
+        assert rel_l2(xs.double().cpu().numpy() * scale, ref) < 1e-4
+
+
 @pytest.mark.parametrize("bin_mm", [1.7, 2.6])
 def test_osl_update_other_bin_pitch(cuda_ok, bin_mm):
     """Bins finer than the voxels (|beta| < 1 at some angles: up to three rays
