@@ -77,8 +77,8 @@ LM_FLOPS_PER_VOXEL_STEP = lm_flops_per_voxel_step(frames=S.WORKLOADS["pr2"].n_fr
 # the kernel's source file is unchanged (sha256 prefix); see profiles/.
 TRAFFIC = {
     "lm_step": {"bytes": 473.62e6 * 127 / 16, "src": "kinetics.cu", "sha": "55a292b0e0d79625"},
-    "bwd_osl": {"bytes": 515.09e6 * 127 / 16, "src": "projector.cu", "sha": "3efd6170d0b11f75"},
-    "fwd_ratio": {"bytes": 264.26e6 * 127 / 16, "src": "projector.cu", "sha": "3efd6170d0b11f75"},
+    "bwd_osl": {"bytes": 515.41e6 * 127 / 16, "src": "projector.cu", "sha": "fe4362dd5524dcb9"},
+    "fwd_ratio": {"bytes": 259.29e6 * 127 / 16, "src": "projector.cu", "sha": "fe4362dd5524dcb9"},
     "tac_eval": {"bytes": 153.51e6 * 127 / 16, "src": "kinetics.cu", "sha": "55a292b0e0d79625"},
 }
 
