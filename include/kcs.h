@@ -407,7 +407,10 @@ int kcs_icm_iterate(kcs_study_t* st, int n_iter, void* stream);
  * stream and overlap the compute: iteration k+1's counts arrive during
  * iteration k's MAP-LM steps (which do not read the counts), iteration k's
  * maps leave during iteration k+1's OSL pass (which does not touch them).
- * Results equal kcs_icm_iterate's bit for bit.  Asynchronous: the caller's
+ * When the rows of a subset are every S-th sinogram row of the volume (the
+ * angle count a multiple of S, or a single plane), the first iteration's
+ * counts come in by one strided copy per subset and its OSL pass waits only
+ * for each subset's own rows.  Results equal kcs_icm_iterate's bit for bit.  Asynchronous: the caller's
  * stream completes after the last copy; the host buffers must stay valid
  * until then.  Host-issued (no graph replay). */
 int kcs_icm_iterate_host(kcs_study_t* st, int n_iter, const void* counts_host,

@@ -22,6 +22,7 @@ struct kcs_study {
   // host I/O of kcs_icm_iterate_host: a private copy stream and its events
   cudaStream_t copy;
   cudaEvent_t ev[4];      // OSL pass done, counts in, fit done, maps out
+  std::vector<cudaEvent_t> ev_sub;   // counts rows of subset k in (first upload of a call)
 };
 
 using namespace kcs;
@@ -36,13 +37,20 @@ int fit_nbhd(const kcs_study_desc_t& d) { return d.neighbourhood == 26 ? 26 : 8;
 // Acceptance threshold of the MAP-LM step: the library default unless given.
 float fit_tau(const kcs_study_desc_t& d) { return d.lm_tau_given ? d.lm_tau : KCS_LM_TAU_DEFAULT; }
 
-int issue_osl_pass(const kcs_study* st, bool prior, void* stream) {
+// wait_sub (optional): one event per subset, waited for before its update.
+int issue_osl_pass(const kcs_study* st, bool prior, void* stream,
+                   const cudaEvent_t* wait_sub = nullptr) {
   const kcs_study_desc_t& d = st->d;
   const kcs_geometry* g = d.geom;
   if (d.method == KCS_METHOD_INDIRECT) prior = false;
   // host-side ranges (visible in Nsight timelines) around the issue of each phase
   nvtxRangePushA("kcs::osl_pass");
   for (int k = 0; k < g->S; ++k) {
+    if (wait_sub && cudaStreamWaitEvent(as_stream(stream), wait_sub[k], 0) != cudaSuccess) {
+      nvtxRangePop();
+      set_error("cudaStreamWaitEvent failed");
+      return KCS_ERR_CUDA;
+    }
     const int rc = kcs_osl_update_ex(g, k, d.n_frames, d.frame_dt, d.kappa, d.counts,
                                      d.counts_type, d.randoms, d.randoms_layout, d.bin_factor,
                                      prior ? d.F : nullptr, prior ? d.beta_kp : 0.f,
@@ -156,6 +164,8 @@ int kcs_destroy_study(kcs_study_t* st) {
     if (st->copy) cudaStreamDestroy(st->copy);
     for (auto e : st->ev)
       if (e) cudaEventDestroy(e);
+    for (auto e : st->ev_sub)
+      if (e) cudaEventDestroy(e);
   }
   delete st;
   return KCS_OK;
@@ -242,7 +252,27 @@ int kcs_icm_iterate_host(kcs_study_t* st, int n_iter, const void* counts_host,
   // the maps) precedes the first copy
   KCS_CUDA(cudaEventRecord(st->ev[FIT_DONE], s));
   KCS_CUDA(cudaStreamWaitEvent(c, st->ev[FIT_DONE], 0));
-  if (counts_host) {
+  // The first upload goes subset by subset when the rows of a subset are
+  // every S-th sinogram row of the volume (A a multiple of S, or one plane):
+  // one strided copy each, and the first OSL pass starts on subset 0 while the
+  // later subsets' rows are still arriving.  Later uploads overlap the fit.
+  const size_t row_bytes = (size_t)g->B * d.n_frames * (d.counts_type == KCS_U16 ? 2 : 4);
+  const bool by_subset = counts_host && g->S > 1 && (g->A % g->S == 0 || g->nz == 1);
+  if (by_subset) {
+    if (st->ev_sub.size() != (size_t)g->S) {
+      st->ev_sub.assign(g->S, nullptr);
+      for (auto& e : st->ev_sub) KCS_CUDA(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+    }
+    for (int k = 0; k < g->S; ++k) {
+      const size_t rows = g->A % g->S == 0 ? (size_t)g->nz * (g->A / g->S)
+                                           : (size_t)subset_count(g, k);
+      KCS_CUDA(cudaMemcpy2DAsync(static_cast<char*>(const_cast<void*>(d.counts)) + k * row_bytes,
+                                 g->S * row_bytes,
+                                 static_cast<const char*>(counts_host) + k * row_bytes,
+                                 g->S * row_bytes, row_bytes, rows, cudaMemcpyHostToDevice, c));
+      KCS_CUDA(cudaEventRecord(st->ev_sub[k], c));
+    }
+  } else if (counts_host) {
     KCS_CUDA(cudaMemcpyAsync(const_cast<void*>(d.counts), counts_host, counts_bytes,
                              cudaMemcpyHostToDevice, c));
   }
@@ -250,12 +280,13 @@ int kcs_icm_iterate_host(kcs_study_t* st, int n_iter, const void* counts_host,
   KCS_CUDA(cudaEventRecord(st->ev[MAPS_OUT], c));
   for (int it = 0; it < n_iter; ++it) {
     const bool prior = prior_on(st);
-    KCS_CUDA(cudaStreamWaitEvent(s, st->ev[COUNTS_IN], 0));   // this iteration's counts
+    const bool sub_wait = by_subset && it == 0;
+    if (!sub_wait) KCS_CUDA(cudaStreamWaitEvent(s, st->ev[COUNTS_IN], 0));   // this iteration's counts
     if (prior && st->iterations == 0) {
       const int rc = launch_tac_eval(d.kin, V, d.params, d.F, nullptr, s);
       if (rc) return rc;
     }
-    int rc = issue_osl_pass(st, prior, s);
+    int rc = issue_osl_pass(st, prior, s, sub_wait ? st->ev_sub.data() : nullptr);
     if (rc) return rc;
     // the next iteration's counts arrive while this one fits the maps (the
     // fit does not read the counts)

@@ -222,6 +222,42 @@ def test_stacked_planes_equal_separate_studies(cuda_ok):
         assert torch.equal(x1[0], xR[r]) and torch.equal(p1[:, 0], pR[:, r])
 
 
+def test_streamed_host_io_subset_copies_multi_plane(cuda_ok):
+    """With the angle count a multiple of the subset count, iterate_host brings
+    the first counts in by one strided copy per subset (the first OSL pass
+    starts on subset 0 while the later rows arrive); three stacked planes and
+    5 subsets of 90 angles give the device-only iterations bit for bit."""
+    import paper_1803_10045_b300 as K
+    P = pr1_problem()
+    W = P["W"]
+    R, S_ = 3, 5
+    assert W.n_angles % S_ == 0
+    kin = K.Kinetics(P["ts"], P["te"], S.FENG)
+    dt = _t(_f32(P["dt"]))
+    kappa = float(np.float32(P["kappa"]))
+    counts = _t(np.concatenate([pr1_problem(r)["counts"] for r in range(R)])).to(torch.uint16)
+    g = K.Geometry(W.nx, W.ny, R, W.vox_mm, W.n_bins, W.n_angles, W.bin_mm, S_)
+    start = _t(np.broadcast_to(np.array(S.XI0)[:, None, None, None], (4, R, W.ny, W.nx)))
+
+    def fresh(cdev):
+        x = K.init_image(g, dt, kappa, counts)
+        p = start.clone()
+        return x, p, K.Study(g, kin, dt, kappa, cdev, x, p, n_lm=10, beta_kp=0.1, beta_h=0.1,
+                             delta=0.01)
+    xa, pa, a = fresh(counts)
+    a.iterate(2)
+    cdev = torch.zeros_like(counts)
+    xb, pb, b = fresh(cdev)
+    ch = torch.empty(counts.shape, dtype=counts.dtype, pin_memory=True)
+    ch.copy_(counts)
+    ph = torch.empty((2, 4, R, W.ny, W.nx), dtype=torch.float32, pin_memory=True)
+    b.iterate_host(2, ch, ph)
+    torch.cuda.synchronize()
+    assert torch.equal(cdev, counts)
+    assert torch.equal(xa, xb) and torch.equal(pa, pb) and torch.equal(a.F, b.F)
+    assert torch.equal(ph[1], pa.cpu())
+
+
 @pytest.mark.parametrize("storage", ["f32", "bf16"])
 def test_checkpoint_resume_is_bit_identical(cuda_ok, tmp_path, storage):
     """4 ICM iterations straight equal 2 iterations, a checkpoint to disk, a
