@@ -104,3 +104,14 @@ def oracle_icm_runs(jobs):
     n = max(1, min(len(jobs), os.cpu_count() or 1))
     with ProcessPoolExecutor(n, mp_context=mp.get_context("spawn")) as ex:
         return list(ex.map(_oracle_icm_job, jobs))
+
+
+def ulp(v, kind):
+    """Spacing of the storage grid of kind ("bf16", "f16" or "f32") at |v|."""
+    v = np.abs(np.asarray(v, np.float64))
+    if kind == "f16":
+        return np.spacing(np.float16(np.minimum(v, 32768))).astype(np.float64)
+    if kind == "bf16":
+        _, e = np.frexp(np.maximum(v, 1e-38))
+        return np.ldexp(1.0, e - 8)
+    return np.spacing(v.astype(np.float32)).astype(np.float64)

@@ -12,7 +12,7 @@ import pytest
 import torch
 
 import kcs_synth as S
-from cases import lm_step_parity, rel_l2
+from cases import lm_step_parity, rel_l2, ulp
 from oracle import kinetics as OK
 from oracle import lm as OL
 from oracle import osl as OO
@@ -63,6 +63,50 @@ def test_full_size_osl_update_planes(cuda_ok, beta):
         e = rel_l2(got[n], ref[n])
         print(f"beta {beta} plane {z}: rel-L2 {e:.2e}")
         assert e < 1e-4
+
+
+@pytest.mark.parametrize("kind", ["bf16", "f16"])
+def test_full_size_stored_osl_update_planes(cuda_ok, kind):
+    """The precision form at full size: the fused OSL update of an image stored
+    as bfloat16 / float16 with a per-frame scale (uint16 counts, the prior on)
+    equals, on three whole planes, the oracle's update with the same stores
+    rounded to the same grid, within one unit in the last place of the
+    storage type."""
+    import paper_1803_10045_b300 as K
+    W = S.WORKLOADS["pr2"]
+    M, k, beta = W.n_frames, 11, 0.05
+    kg = K.Geometry(W.nx, W.ny, W.nz, W.vox_mm, W.n_bins, W.n_angles, W.bin_mm, W.n_subsets)
+    og = OP.Geometry(W.nx, W.ny, W.vox_mm, W.n_bins, W.n_angles, W.bin_mm, W.n_subsets)
+    ts, te = W.frames()
+    dt = np.asarray(te - ts, np.float32)
+    kappa = _f32(2e-3)
+    gen = torch.Generator(device="cuda").manual_seed(13)
+    shape = (W.nz, W.ny, W.nx, M)
+    x = 0.5 + 2.0 * torch.rand(shape, device="cuda", generator=gen)
+    F = x * (0.8 + 0.4 * torch.rand(shape, device="cuda", generator=gen))
+    counts_i = torch.randint(0, 12, (W.nz, W.n_angles, W.n_bins, M), device="cuda",
+                             generator=gen, dtype=torch.int32)
+    counts = counts_i.to(torch.uint16)
+    r = (0.05 * dt).astype(np.float32)
+    scale = x.reshape(-1, M).amax(0)                        # per-frame level, float32
+    xs = (x / scale).to({"bf16": torch.bfloat16, "f16": torch.float16}[kind])
+    del x
+    zs = [0, 63, 126]
+    ang = torch.as_tensor(og.subsets[k], device="cuda")
+    xs0 = xs[zs].double().cpu().numpy()
+    F0 = F[zs].double().cpu().numpy()
+    c0 = counts_i[zs][:, ang].double().cpu().numpy()
+    del counts_i
+    sc = scale.double().cpu().numpy()
+    K.osl_update(kg, k, xs, torch.tensor(dt, device="cuda"), kappa, counts,
+                 torch.tensor(r, device="cuda"), None, F, beta, 1.0, x_scale=scale)
+    got = xs[zs].double().cpu().numpy()
+    ref = OO.osl_update_stored(og, xs0, k, c0, kappa, dt.astype(np.float64), sc, kind,
+                               randoms_k=r.astype(np.float64), F=F0, beta=beta)
+    nulp = np.abs(got - ref) / ulp(ref, kind)
+    print(f"{kind}: max {nulp.max():.2f} ulp, {np.mean(nulp > 0):.3%} of values differ")
+    assert nulp.max() <= 1.0 + 1e-9
+    assert np.mean(nulp > 0) < 0.02
 
 
 def test_full_size_lm_step_sampled_voxels(cuda_ok):

@@ -22,7 +22,7 @@ import torch
 import kcs_synth as S
 from oracle import kinetics as OK
 from oracle import osl as OO
-from cases import oracle_icm_runs, pr1_problem, rel_l2
+from cases import oracle_icm_runs, pr1_problem, rel_l2, ulp
 
 pytestmark = pytest.mark.gpu
 KINDS = {"f32": torch.float32, "bf16": torch.bfloat16, "f16": torch.float16}
@@ -36,14 +36,7 @@ def _f32(a):
     return np.asarray(a, np.float32).astype(np.float64)
 
 
-def _ulp(v, kind):
-    v = np.abs(np.asarray(v, np.float64))
-    if kind == "f16":
-        return np.spacing(np.float16(np.minimum(v, 32768))).astype(np.float64)
-    if kind == "bf16":
-        _, e = np.frexp(np.maximum(v, 1e-38))
-        return np.ldexp(1.0, e - 8)
-    return np.spacing(v.astype(np.float32)).astype(np.float64)
+_ulp = ulp
 
 
 def _setup():
