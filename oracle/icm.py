@@ -18,10 +18,15 @@ fit) and KCS DIRECT (the full ICM).
 ICM on this joint objective is not convex and the paper defines no stopping
 rule, so parity is on the trajectory for fixed iteration counts.
 
-Parity status: icm() itself is parity unpinned -- nothing outside the oracle
-fixes the trajectory of the alternation (the paper prints no values).  It
-only composes osl.osl_pass and lm.lm_fit, which are pinned in
-tests/test_oracle_osl.py and tests/test_oracle_lm.py.
+Parity status: the paper prints no trajectory, so icm() is pinned by an
+invariant and by its parts: noise-free data of a phantom with uniform kinetic
+maps is a fixed point of the whole alternation (every ratio is 1, the prior
+term vanishes at x = F, the LM residual and the Huber gradient are zero), and
+a perturbed start is not (tests/test_oracle_osl.py); it composes
+osl.osl_pass and lm.lm_fit, which are pinned in tests/test_oracle_osl.py and
+tests/test_oracle_lm.py, in the order the composition test checks.  The
+invariant does not fix the sign of the prior term (it vanishes there); the
+OSL pins do.
 """
 from __future__ import annotations
 

@@ -137,3 +137,31 @@ def test_icm_methods_compose_as_defined():
     xd, xid, _, _ = icm.icm(g, counts, kappa, ts, te, S.FENG, 2, 2, 0.1, 0.1, 0.01, method="direct")
     xk, xik, _, _ = icm.icm(g, counts, kappa, ts, te, S.FENG, 2, 2, 0.1, 0.0, 0.01, method="kcs")
     assert np.array_equal(xd, xk) and np.array_equal(xid, xik)
+
+
+def test_icm_noise_free_fixed_point():
+    """Noise-free data of a phantom with uniform kinetic maps is a fixed point
+    of the whole ICM (Sec. II-D): started from those maps and their model
+    TACs, every ratio s / ybar is 1, so each OSL update returns the image (the
+    back-projected ones equal the sensitivity, and the prior term vanishes
+    where x = F); the LM residual and the Huber gradient of uniform maps are
+    zero, so the fit keeps the maps.  A wrong sensitivity, kappa or frame
+    duration anywhere in the update would move the image off the point."""
+    import kcs_synth as S
+    from oracle import icm, kinetics
+    g = P.Geometry(16, 16, 2.0, 26, 12, 2.0, 3)
+    ts, te = S.schedule([(2, 30), (2, 120), (2, 300)])
+    dt = te - ts
+    xi = np.broadcast_to(np.array(S.CLASS_XI["gm"], float)[:, None, None, None],
+                         (4, 1, 16, 16)).copy()
+    F = kinetics.model_maps(xi, ts, te, S.FENG)
+    kappa = 0.7
+    counts = g.forward(F) * kappa * dt
+    x, xi_out, _, _ = icm.icm(g, counts, kappa, ts, te, S.FENG, 3, 4, 0.5, 0.5, 0.01,
+                              x0=F.copy(), xi0=xi.copy())
+    assert np.max(np.abs(x - F) / F) < 1e-9
+    assert np.max(np.abs(xi_out - xi) / xi) < 1e-9
+    # the same data with the image perturbed is not a fixed point
+    x2, _, _, _ = icm.icm(g, counts, kappa, ts, te, S.FENG, 1, 4, 0.5, 0.5, 0.01,
+                          x0=F * 1.01, xi0=xi.copy())
+    assert np.max(np.abs(x2 - F * 1.01) / F) > 1e-4
