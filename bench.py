@@ -46,13 +46,18 @@ WORKLOAD = "PR2: 344x344x127 (2.09 mm), 344 bins x 252 angles, 24 frames, 21 sub
 N_LM = 10
 BETA_H, DELTA = 0.1, 0.01
 # The kinetics-derived prior competes with kappa dt sens in the OSL denominator,
-# so its weight scales with the count calibration: beta_kp = 0.1 kappa / kappa_PR1
-# gives PR2 the prior-to-data ratio of config PR1 (beta_kp = 0.1 at kappa ~ 5e-3).
+# so its weight scales with the count calibration.  Linearised at x = F, one
+# OSL update multiplies a deviation x - F by 1 - r with
+# r = beta_kp F / (S sigma2 kappa dt sens): the update is stable only for
+# r < 2, and the short early frames of PR2 at its hottest voxels reached
+# r = 2.3 with beta_kp = 0.1 kappa / kappa_PR1.  beta_kp = 0.01 kappa /
+# kappa_PR1 (the prior-to-data ratio of the end-to-end parity tests' stable
+# weight on config PR1, beta_kp = 0.01 at kappa ~ 5e-3) keeps r below 0.25.
 KAPPA_PR1 = 5.06e-3
 
 
 def beta_kp_for(kappa):
-    return 0.1 * kappa / KAPPA_PR1
+    return 0.01 * kappa / KAPPA_PR1
 FP32_LANES_PER_SM, N_SM = 128, 148
 
 

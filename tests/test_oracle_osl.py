@@ -165,3 +165,31 @@ def test_icm_noise_free_fixed_point():
     x2, _, _, _ = icm.icm(g, counts, kappa, ts, te, S.FENG, 1, 4, 0.5, 0.5, 0.01,
                           x0=F * 1.01, xi0=xi.copy())
     assert np.max(np.abs(x2 - F * 1.01) / F) > 1e-4
+
+
+def test_osl_prior_linear_response():
+    """The kinetics prior in one OSL update (Eq. 2-3), to first order: at
+    x = F (1 + eps) in one voxel v, the update with weight beta shrinks the
+    deviation by r = (beta / S) F / (sigma2 kappa dt sens_k[v]) more than the
+    update without the prior -- the factor that decides the stability of the
+    one-step-late update (|1 - r| < 1).  Fixes the sign of the prior term,
+    its 1 / S per subset and its sigma2."""
+    import kcs_synth as S
+    from oracle import kinetics
+    g = P.Geometry(16, 16, 2.0, 26, 12, 2.0, 3)
+    ts, te = S.schedule([(2, 30), (2, 120)])
+    dt = te - ts
+    xi = np.broadcast_to(np.array(S.CLASS_XI["gm"], float)[:, None, None, None],
+                         (4, 1, 16, 16)).copy()
+    F = kinetics.model_maps(xi, ts, te, S.FENG)
+    kappa, eps, k, v = 0.7, 1e-6, 1, (0, 8, 7)
+    counts_k = osl.subset_slice(g.forward(F) * kappa * dt, g, k)
+    x = F.copy()
+    x[v] *= 1 + eps
+    sens = g.back(np.ones(counts_k.shape[:-1] + (1,)), k)[..., 0]   # P_k^T 1
+    x0 = osl.osl_update(g, x, k, counts_k, kappa, dt)
+    for beta, sigma2 in ((0.3, 1.0), (0.3, 2.0), (1.2, 1.0)):
+        xb = osl.osl_update(g, x, k, counts_k, kappa, dt, None, None, F, beta, sigma2)
+        shrink = ((x0[v] - F[v]) - (xb[v] - F[v])) / (F[v] * eps)
+        r = (beta / g.n_subsets) * F[v] / (sigma2 * kappa * dt * sens[v])
+        assert np.allclose(shrink, r, rtol=1e-4), (beta, sigma2, shrink, r)
