@@ -196,9 +196,27 @@ __device__ __forceinline__ void fwd_epilogue(const ProjArgs& p, float4 acc, floa
 // Forward projection of every frame of rays (z, ak, b); RATIO replaces the
 // projection by rho = s / (kappa dt n_d (P x) + r).
 constexpr int FWD_THREADS = 128;   // 4 warps per block (measured best of 64..512)
+// Register budget and steps per trip of the march, by image storage type.
+// Float32: 8 blocks per SM, a 64-register budget that keeps 8 steps' loads
+// in flight (1.50 ms per subset at full size, against 1.68 ms with the
+// default budget of 40 registers and 4 steps; 6-10 blocks and 4-12 steps
+// measured 1.50-1.56 ms).  16-bit storage: the widening needs registers of
+// its own (8 steps at 64 registers spilled 180 bytes and took 3.3 ms).
+#ifndef KCS_FWD16_MIN_BLOCKS
+#define KCS_FWD16_MIN_BLOCKS 1
+#endif
+template <class TX> struct FwdTune {
+  static constexpr int min_blocks = 8, steps = 8;
+};
+template <> struct FwdTune<__nv_bfloat16> {
+  static constexpr int min_blocks = KCS_FWD16_MIN_BLOCKS, steps = 4;
+};
+template <> struct FwdTune<__half> {
+  static constexpr int min_blocks = KCS_FWD16_MIN_BLOCKS, steps = 4;
+};
 
 template <int MQ, bool RATIO, class TX, class TC, class TY>
-__global__ void __launch_bounds__(FWD_THREADS) k_forward(ProjArgs p) {
+__global__ void __launch_bounds__(FWD_THREADS, FwdTune<TX>::min_blocks) k_forward(ProjArgs p) {
   constexpr int RPW = 32 / MQ;
   const int lane = threadIdx.x & 31;
   const int sub = lane / MQ;
@@ -226,11 +244,11 @@ __global__ void __launch_bounds__(FWD_THREADS) k_forward(ProjArgs p) {
   // test is repeated per step below.
   int t0, t1;
   ray_range(bf, T, n_major, n_minor, centre, tc, t0, t1);
-  // Branch-free march, 4 steps per trip: out-of-grid partners are predicated
+  // Branch-free march, U steps per trip: out-of-grid partners are predicated
   // loads of zero (their weight is exactly 0), so several steps' loads are in
   // flight at once and the accumulated values equal the plain loop's.
   float4 acc = f4(0.f);
-  constexpr int U = 4;
+  constexpr int U = FwdTune<TX>::steps;
   const unsigned nmin = (unsigned)n_minor;
   // per trip: the centred major coordinate of its first step (exact: small
   // integers and half-integers) and the image row/column of that step; within
