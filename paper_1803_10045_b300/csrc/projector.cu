@@ -201,18 +201,23 @@ constexpr int FWD_THREADS = 128;   // 4 warps per block (measured best of 64..51
 // in flight (1.50 ms per subset at full size, against 1.68 ms with the
 // default budget of 40 registers and 4 steps; 6-10 blocks and 4-12 steps
 // measured 1.50-1.56 ms).  16-bit storage: the widening needs registers of
-// its own (8 steps at 64 registers spilled 180 bytes and took 3.3 ms).
+// its own; the default budget (63 registers) with 4 steps is best (bf16
+// 1.47 ms; 6 or 8 steps at 78-96 registers 1.58-1.63 ms, 8 steps at 64
+// registers spilled 180 bytes and took 3.3 ms).
 #ifndef KCS_FWD16_MIN_BLOCKS
 #define KCS_FWD16_MIN_BLOCKS 1
+#endif
+#ifndef KCS_FWD16_STEPS
+#define KCS_FWD16_STEPS 4
 #endif
 template <class TX> struct FwdTune {
   static constexpr int min_blocks = 8, steps = 8;
 };
 template <> struct FwdTune<__nv_bfloat16> {
-  static constexpr int min_blocks = KCS_FWD16_MIN_BLOCKS, steps = 4;
+  static constexpr int min_blocks = KCS_FWD16_MIN_BLOCKS, steps = KCS_FWD16_STEPS;
 };
 template <> struct FwdTune<__half> {
-  static constexpr int min_blocks = KCS_FWD16_MIN_BLOCKS, steps = 4;
+  static constexpr int min_blocks = KCS_FWD16_MIN_BLOCKS, steps = KCS_FWD16_STEPS;
 };
 
 template <int MQ, bool RATIO, class TX, class TC, class TY>
