@@ -433,14 +433,16 @@ __global__ void k_huber_grad(int nx, int ny, int nz, const float* p, float delta
 #ifndef KCS_LM_CARVEOUT
 #define KCS_LM_CARVEOUT 50   // percent of the maximum shared memory per SM
 #endif
-// frames per trip of the model loop in the LM kernels: 2 (64 registers),
-// 1 % faster than 1 now that the table reads are served from L2; 80
-// registers for 6 blocks per SM lose 20 %, 2 voxels per thread 80 %
+// frames per trip of the model loop in the LM kernels: 2, 1 % faster than 1
+// now that the table reads are served from L2.  Blocks per SM: 7 (a
+// 72-register budget), 1.94 vs 1.98 ms per step at 8 blocks (64 registers);
+// 7 blocks with 3 or 4 frames per trip 1.97 / 1.96, 6 blocks (80 registers)
+// 20 % slower, 2 voxels per thread 80 %
 #ifndef KCS_LM_UNROLL
 #define KCS_LM_UNROLL 2
 #endif
 #ifndef KCS_LM_MINBLOCKS
-#define KCS_LM_MINBLOCKS 8
+#define KCS_LM_MINBLOCKS 7
 #endif
 constexpr int LM_THREADS = 128;
 constexpr int LM_VPT = KCS_LM_VPT;              // voxels per thread
