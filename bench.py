@@ -82,8 +82,8 @@ LM_FLOPS_PER_VOXEL_STEP = lm_flops_per_voxel_step(frames=S.WORKLOADS["pr2"].n_fr
 # the kernel's source file is unchanged (sha256 prefix); see profiles/.
 TRAFFIC = {
     "lm_step": {"bytes": 473.66e6 * 127 / 16, "src": "kinetics.cu", "sha": "94e46969dddda74f"},
-    "bwd_osl": {"bytes": 515.07e6 * 127 / 16, "src": "projector.cu", "sha": "e8d98b7b73ffad96"},
-    "fwd_ratio": {"bytes": 211.53e6 * 127 / 16, "src": "projector.cu", "sha": "e8d98b7b73ffad96"},
+    "bwd_osl": {"bytes": 515.07e6 * 127 / 16, "src": "projector.cu", "sha": "9749039f5d8668f2"},
+    "fwd_ratio": {"bytes": 211.53e6 * 127 / 16, "src": "projector.cu", "sha": "9749039f5d8668f2"},
     "tac_eval": {"bytes": 153.52e6 * 127 / 16, "src": "kinetics.cu", "sha": "94e46969dddda74f"},
 }
 

@@ -1102,7 +1102,7 @@ static ProjArgs base_args(const kcs_geometry* g, int subset) {
 }
 
 // The staged forward is built but off: measured at full size (PR2, float32)
-// it takes 3.28 ms per subset against 1.68 ms for k_forward, bit-identical.
+// it takes 3.28 ms per subset against 1.49 ms for k_forward, bit-identical.
 // Each block re-stages a window overlapping its neighbours' (more bytes from
 // L2 than the L1 misses of k_forward) and waits for its copies at every chunk
 // with fewer warps per SM.  Build with -DKCS_FWD_STAGED=1 to select it.
